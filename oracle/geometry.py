@@ -1,0 +1,155 @@
+"""Closest-point functions cp(x) and squared distances (Sec. 2.1).
+
+TEST INFRASTRUCTURE ONLY (see the package header): the product path never
+imports this module.
+
+cp(x) is the point of the surface S nearest to x in Euclidean distance, well
+defined inside a tube B(S) around S (Sec. 2.1).  Every function here takes an
+(N, d) float64 array of grid-node coordinates and returns ``(cp, dist2)``:
+the closest points (N, d) and the squared distances |x - cp(x)|^2 (N,).
+
+Floating-point evaluation order is fixed and written out operation by
+operation (numpy never fuses a multiply and an add), because the band is the
+set {x : dist2(x) <= lambda^2 dx^2} and band membership is compared bit for
+bit with the CUDA path:
+
+* circle / sphere (centre 0, radius R):
+      r   = sqrt((x0*x0 + x1*x1) + x2*x2)
+      d   = r - R ;  dist2 = d*d
+      t   = R / r ;  cp_a = x_a * t
+* torus about the z axis (major radius R, minor radius r):  Sec. 4.5.4 gives
+  the parametrisation; the closest point is the nearest point of the tube
+  circle of the nearest point of the centre circle:
+      rho = sqrt(x*x + y*y) ; a = rho - R ; q = sqrt(a*a + z*z)
+      d   = q - r ;  dist2 = d*d
+      s   = r / q ;  m = R + a*s ;  k = m / rho
+      cp  = (x*k, y*k, z*s)
+* ellipsoid with semi-axes (a0, a1, a2): cp_i = a_i^2 x_i / (a_i^2 + t) where
+  t is the root, t > -min(a_i^2), of  sum_i a_i^2 x_i^2 / (a_i^2 + t)^2 = 1
+  (the Lagrange condition for minimising |y - x|^2 on the surface).  The
+  oracle finds t by plain bisection to the last bit (slow, obviously
+  convergent: the function is strictly decreasing on that interval).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+CIRCLE, SPHERE, TORUS, ELLIPSOID = "circle", "sphere", "torus", "ellipsoid"
+
+
+@dataclass(frozen=True)
+class Surface:
+    """A closed curve (d = 2) or surface (d = 3) with a closed-form cp."""
+
+    kind: str
+    params: tuple = field(default_factory=tuple)
+
+    @property
+    def dim(self) -> int:
+        return 2 if self.kind == CIRCLE else 3
+
+    @property
+    def reach(self) -> float:
+        """Smallest radius of curvature: the tube B(S) on which cp is unique."""
+        if self.kind in (CIRCLE, SPHERE):
+            return float(self.params[0])
+        if self.kind == TORUS:
+            R, r = self.params
+            return float(min(r, R - r))
+        if self.kind == ELLIPSOID:
+            a = sorted(self.params)
+            return float(a[0] ** 2 / a[-1])
+        raise ValueError(self.kind)
+
+
+def circle(R: float = 1.0) -> Surface:
+    return Surface(CIRCLE, (float(R),))
+
+
+def sphere(R: float = 1.0) -> Surface:
+    return Surface(SPHERE, (float(R),))
+
+
+def torus(R: float, r: float) -> Surface:
+    return Surface(TORUS, (float(R), float(r)))
+
+
+def ellipsoid(a0: float, a1: float, a2: float) -> Surface:
+    return Surface(ELLIPSOID, (float(a0), float(a1), float(a2)))
+
+
+def _round_sphere(X: np.ndarray, R: float):
+    if X.shape[1] == 2:
+        r = np.sqrt(X[:, 0] * X[:, 0] + X[:, 1] * X[:, 1])
+    else:
+        r = np.sqrt((X[:, 0] * X[:, 0] + X[:, 1] * X[:, 1]) + X[:, 2] * X[:, 2])
+    d = r - R
+    dist2 = d * d
+    with np.errstate(divide="ignore", invalid="ignore"):
+        t = R / r
+    cp = X * t[:, None]
+    return cp, dist2
+
+
+def _torus(X: np.ndarray, R: float, r: float):
+    x, y, z = X[:, 0], X[:, 1], X[:, 2]
+    rho = np.sqrt(x * x + y * y)
+    a = rho - R
+    q = np.sqrt(a * a + z * z)
+    d = q - r
+    dist2 = d * d
+    with np.errstate(divide="ignore", invalid="ignore"):
+        s = r / q
+        m = R + a * s
+        k = m / rho
+    cp = np.stack([x * k, y * k, z * s], axis=1)
+    return cp, dist2
+
+
+def _ellipsoid_t(X: np.ndarray, axes: np.ndarray, iters: int = 1100) -> np.ndarray:
+    """Root t of F(t) = sum a_i^2 x_i^2/(a_i^2+t)^2 - 1 by bisection.
+
+    F is strictly decreasing on (-min a_i^2, inf).  Bracket: lower end just
+    above -min a_i^2 (F -> +inf there unless the matching x_i vanish), upper
+    end max a_i |x| (F < 0 there).  Bisection runs until the bracket stops
+    shrinking in float64.
+    """
+    a2 = axes * axes
+    amin2 = a2.min()
+    ax = np.abs(X) * axes[None, :]
+    lo = np.full(X.shape[0], -amin2)
+    hi = np.sqrt((ax * ax).sum(axis=1)) + 1e-300
+    for _ in range(iters):
+        mid = 0.5 * (lo + hi)
+        if np.all((mid == lo) | (mid == hi)):
+            break
+        g = ax / (a2[None, :] + mid[:, None])
+        F = (g * g).sum(axis=1) - 1.0
+        pos = F > 0
+        lo = np.where(pos, mid, lo)
+        hi = np.where(pos, hi, mid)
+    return 0.5 * (lo + hi)
+
+
+def _ellipsoid(X: np.ndarray, axes):
+    axes = np.asarray(axes, dtype=np.float64)
+    t = _ellipsoid_t(X, axes)
+    a2 = axes * axes
+    cp = a2[None, :] * X / (a2[None, :] + t[:, None])
+    diff = X - cp
+    dist2 = (diff[:, 0] * diff[:, 0] + diff[:, 1] * diff[:, 1]) + diff[:, 2] * diff[:, 2]
+    return cp, dist2
+
+
+def closest_point(surface: Surface, X: np.ndarray):
+    """(cp, dist2) of the grid nodes X, shape (N, d), float64."""
+    X = np.asarray(X, dtype=np.float64)
+    if surface.kind in (CIRCLE, SPHERE):
+        return _round_sphere(X, surface.params[0])
+    if surface.kind == TORUS:
+        return _torus(X, *surface.params)
+    if surface.kind == ELLIPSOID:
+        return _ellipsoid(X, surface.params)
+    raise ValueError(surface.kind)

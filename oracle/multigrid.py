@@ -1,0 +1,175 @@
+"""Closest Point Method V-cycle (Sec. 4, Algorithm 4.1) and the outer loop.
+
+TEST INFRASTRUCTURE ONLY (see the package header).
+
+Levels.  Level 0 is the finest grid (dx), level l has spacing dx * 2^l and a
+band of its own built with the same lambda (Sec. 4.3: "bandwidths shrinking
+proportional to the grid sizes"); the coarsest level K is solved directly.
+The grids are nested because every spacing divides 2 (lo = -2).
+
+Transfers (Sec. 4.3).  Restriction E_h^{2h}: each coarse band point takes the
+value at its closest point, interpolated (degree ``transfer_p``, linear by
+default as in Sec. 4.5) from the fine band.  Prolongation E_{2h}^h: each fine
+band point takes the value at its closest point interpolated from the coarse
+band.  No full-weighting factor.  Coarse operators are rediscretised:
+A^{2h} = c I - M^{2h}.
+
+Smoothers.
+* ``rm``       Ruuth-Merriman Jacobi (Eq. 4.2): u += omega diag(At)^-1 (f - At u)
+               with At = cI - L (band-restricted L), then u := E u.  The residual
+               restricted in step 2 of Algorithm 4.1 is f - At u.
+* ``jacobi``   standard Jacobi on A (Eq. 4.1): u += omega diag(A)^-1 (f - A u);
+               the residual restricted in step 2 is f - A (E u) (Sec. 4.4).
+The paper uses omega = 1 with nu1 = nu2 = 3 (Sec. 4.5); the defaults here are
+omega = 2/3 and nu1 = nu2 = 2.
+
+V-cycle (Algorithm 4.1): nu1 smoothing steps, residual, restriction, either
+the direct coarsest solve or a recursive V-cycle from zero, prolongation and
+correction, nu2 smoothing steps.
+
+Outer loop.  Defect correction in float64:  r = f - A u  (A in the form of
+``operators``), stop when ||r||_inf <= tol ||f||_inf, else u += V(0, r).
+(The paper stops on the relative change of u, 1e-6; the relative residual is
+the criterion used throughout this project.)
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+
+from .band import Band, build_band
+from .geometry import Surface
+from .interp import interp_matrix
+from .operators import Operators
+
+
+@dataclass
+class Level:
+    band: Band
+    ops: Operators
+    c: np.ndarray                     # per-point c on this level
+    R: object = None                  # restriction from this level to the next coarser
+    P: object = None                  # prolongation from the next coarser to this level
+    diagA: np.ndarray | None = None   # c - diag(M)
+
+
+@dataclass
+class MGOptions:
+    nu1: int = 2
+    nu2: int = 2
+    omega: float = 2.0 / 3.0
+    smoother: str = "rm"              # "rm" | "jacobi"
+    transfer_p: int = 1
+    p: int = 3
+
+
+@dataclass
+class Hierarchy:
+    levels: list
+    opts: MGOptions
+    lu: tuple = field(default=None)
+
+    @property
+    def fine(self) -> Level:
+        return self.levels[0]
+
+
+def coarsest_spacing_ok(surface: Surface, dx: float, lambda2: float) -> bool:
+    """Coarsening rule: (lambda + 1) dx < reach, so cp is unique on B+."""
+    return (np.sqrt(lambda2) + 1.0) * dx < surface.reach
+
+
+def build_hierarchy(surface: Surface, dx: float, coarsest_dx: float, c=1.0,
+                    opts: MGOptions | None = None, c_fn=None) -> Hierarchy:
+    """Levels dx, 2dx, .., coarsest_dx.  ``c_fn(cp) -> c`` gives a variable c."""
+    opts = opts or MGOptions()
+    levels = []
+    h = dx
+    while True:
+        band = build_band(surface, h, p=opts.p)
+        ops = Operators(band, opts.p)
+        cvec = c_fn(band.cp[: band.nb]) if c_fn is not None else np.full(band.nb, float(c))
+        levels.append(Level(band, ops, cvec))
+        if h >= coarsest_dx * (1 - 1e-12):
+            break
+        h *= 2.0
+    for l in range(len(levels) - 1):
+        fine, coarse = levels[l], levels[l + 1]
+        fine.R = interp_matrix(fine.band, coarse.band.cp[: coarse.band.nb], opts.transfer_p)
+        fine.P = interp_matrix(coarse.band, fine.band.cp[: fine.band.nb], opts.transfer_p)
+    for lev in levels:
+        lev.diagA = lev.c - lev.ops.diag_M()
+    hier = Hierarchy(levels, opts)
+    last = levels[-1]
+    hier.lu = sla.lu_factor(last.ops.A_matrix(last.c).toarray())
+    return hier
+
+
+def smooth(hier: Hierarchy, l: int, u: np.ndarray, f: np.ndarray) -> np.ndarray:
+    lev, o = hier.levels[l], hier.opts
+    if o.smoother == "rm":
+        u = u + o.omega * (f - lev.ops.apply_Atilde(u, lev.c)) / lev.ops.diag_Atilde(lev.c)
+        return lev.ops.extend(u)[: lev.ops.nb]
+    if o.smoother == "jacobi":
+        return u + o.omega * (f - lev.ops.apply_A(u, lev.c)) / lev.diagA
+    raise ValueError(o.smoother)
+
+
+def transfer_residual(hier: Hierarchy, l: int, u: np.ndarray, f: np.ndarray) -> np.ndarray:
+    lev, o = hier.levels[l], hier.opts
+    if o.smoother == "rm":
+        return f - lev.ops.apply_Atilde(u, lev.c)
+    wb = lev.ops.extend(u)[: lev.ops.nb]
+    return f - lev.ops.apply_A(wb, lev.c)
+
+
+def coarse_solve(hier: Hierarchy, f: np.ndarray) -> np.ndarray:
+    return sla.lu_solve(hier.lu, f)
+
+
+def vcycle(hier: Hierarchy, u: np.ndarray, f: np.ndarray, l: int = 0) -> np.ndarray:
+    """One V-cycle V^h(u, f) of Algorithm 4.1 on level l."""
+    o = hier.opts
+    if l == len(hier.levels) - 1:
+        return coarse_solve(hier, f)
+    for _ in range(o.nu1):
+        u = smooth(hier, l, u, f)
+    r = transfer_residual(hier, l, u, f)
+    lev = hier.levels[l]
+    fc = lev.R @ r
+    if l + 1 == len(hier.levels) - 1:
+        uc = coarse_solve(hier, fc)
+    else:
+        uc = vcycle(hier, np.zeros_like(fc), fc, l + 1)
+    u = u + lev.P @ uc
+    for _ in range(o.nu2):
+        u = smooth(hier, l, u, f)
+    return u
+
+
+@dataclass
+class SolveReport:
+    iters: int
+    history: list
+    converged: bool
+
+
+def solve(hier: Hierarchy, f: np.ndarray, tol: float = 1e-10, max_iter: int = 100,
+          u0: np.ndarray | None = None) -> tuple[np.ndarray, SolveReport]:
+    """Outer defect correction: u += V(0, f - A u) until ||r||/||f|| <= tol."""
+    fine = hier.fine
+    u = np.zeros_like(f) if u0 is None else u0.copy()
+    fn = np.abs(f).max()
+    hist = []
+    for it in range(max_iter + 1):
+        r = fine.ops.residual(u, f, fine.c)
+        rel = np.abs(r).max() / fn
+        hist.append(rel)
+        if rel <= tol:
+            return u, SolveReport(it, hist, True)
+        if it == max_iter:
+            break
+        u = u + vcycle(hier, np.zeros_like(r), r)
+    return u, SolveReport(max_iter, hist, False)

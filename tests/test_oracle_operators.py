@@ -1,0 +1,154 @@
+"""Pins of the oracle's operators against the paper and the mathematics (CPU only)."""
+import itertools
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from conftest import load_golden
+from oracle.band import build_band, stencil
+from oracle.geometry import circle, sphere
+from oracle.interp import interp_matrix, lagrange_1d
+from oracle.operators import Operators, gamma, paper_M
+import synth
+
+
+def _brute_force_M_row(band, i, p=3):
+    """Row i of M = diag(L) + (L - diag L) E by direct evaluation of the definition.
+
+    Independent of the assembled path: loops over the 2d neighbours k of node
+    i and over the (p+1)^d stencil nodes of cp(x_k), weights from the explicit
+    cubic Lagrange products.
+    """
+    d, h2 = band.dim, band.dx * band.dx
+    row = {i: -2.0 * d / h2}
+    own = band.coords_of(band.keys[i:i + 1])[0]
+    for a in range(d):
+        for sgn in (-1, 1):
+            nb = own.copy()
+            nb[a] += sgn
+            k = band.index_in_bplus(band.key_of(nb[None, :]))[0]
+            y = band.cp[k]
+            t = (y - band.lo) / band.dx
+            fl = np.floor(t)
+            s = t - fl
+            w1 = []
+            for ax in range(d):
+                sa = s[ax]
+                w1.append([-sa * (sa - 1) * (sa - 2) / 6, (sa + 1) * (sa - 1) * (sa - 2) / 2,
+                           -(sa + 1) * sa * (sa - 2) / 2, (sa + 1) * sa * (sa - 1) / 6])
+            for off in itertools.product(range(4), repeat=d):
+                node = fl.astype(np.int64) - 1 + np.asarray(off)
+                j = band.index_in_band(band.key_of(node[None, :]))[0]
+                w = 1.0
+                for ax in range(d):
+                    w *= w1[ax][off[ax]]
+                row[j] = row.get(j, 0.0) + w / h2
+    return row
+
+
+def test_M_matches_brute_force_definition():
+    for surf, dx in [(circle(), 1 / 16), (sphere(), 1 / 8)]:
+        band = build_band(surf, dx)
+        M = Operators(band).M
+        rng = np.random.default_rng(0)
+        for i in rng.choice(band.nb, 25, replace=False):
+            ref = _brute_force_M_row(band, i)
+            got = M.getrow(i).toarray().ravel()
+            want = np.zeros(band.nb)
+            for j, v in ref.items():
+                want[j] = v
+            assert np.abs(got - want).max() <= 1e-10 * np.abs(want).max()
+
+
+def test_row_sums_zero():
+    """Each row of M sums to zero (Theorem 3.3, step 1), so A 1 = c 1."""
+    for surf, dx in [(circle(), 1 / 32), (sphere(), 1 / 16)]:
+        band = build_band(surf, dx)
+        op = Operators(band)
+        one = np.ones(band.nb)
+        assert np.abs(op.apply_M(one)).max() < 1e-9 * op.gamma * 1e-3
+        assert np.abs(op.M @ one).max() < 1e-12 * op.gamma * 10
+
+
+def test_difference_form_equals_assembled():
+    band = build_band(sphere(), 1 / 16)
+    op = Operators(band)
+    u = synth.random_band_vector(band.nb, 5)
+    ref = op.M @ u
+    assert np.abs(op.apply_M(u) - ref).max() <= 1e-13 * np.abs(ref).max()
+    assert np.abs(op.diag_M() - op.M.diagonal()).max() <= 1e-13 * op.gamma
+
+
+def test_M_on_spherical_harmonic_closed_form():
+    """M applied to the cp-extension of Y_lm is the Cartesian Laplacian of
+    Y_lm(x/|x|), i.e. -l(l+1) Y_lm / |x|^2 (Eq. 2.10 applies Delta to u(cp(x))),
+    to O(dx^2) (Remark 3.2: cubic E in both terms is second order)."""
+    errs = []
+    for dx in [1 / 16, 1 / 32, 1 / 64]:
+        band = build_band(sphere(), dx)
+        op = Operators(band)
+        y = band.cp[: band.nb]
+        r2 = (band.points(band.keys) ** 2).sum(1)
+        u = synth.real_sph_harm(3, 2, y)
+        errs.append(np.abs(op.apply_M(u) + 12 * u / r2).max() / 12)
+    assert errs[-1] < 3e-4
+    order = np.log2(np.asarray(errs[:-1]) / np.asarray(errs[1:]))
+    assert np.all(order > 1.8), order
+
+
+def test_M_on_circle_mode_closed_form():
+    """Circle: M (cos(k theta) extended) -> -k^2 cos(k theta) / |x|^2 at O(dx^2)."""
+    errs = []
+    for dx in [1 / 16, 1 / 32, 1 / 64, 1 / 128]:
+        band = build_band(circle(), dx)
+        op = Operators(band)
+        u, _ = synth.circle_mode(band.cp[: band.nb], 4)
+        r2 = (band.points(band.keys) ** 2).sum(1)
+        errs.append(np.abs(op.apply_M(u) + 16 * u / r2).max() / 16)
+    order = np.log2(np.asarray(errs[:-1]) / np.asarray(errs[1:]))
+    assert np.all(order[1:] > 1.8), order
+
+
+def test_gamma():
+    band = build_band(sphere(), 1 / 8)
+    assert gamma(band) == 6 * 64.0
+
+
+def test_paper_form_M_matrix_2d():
+    """Theorem 3.3: in 2-D, A = cI - (E_1 L - 4/dx^2 (I - E_3)) is an M-matrix
+    with row sums c (off-diagonals of M >= 0, diagonal < 0)."""
+    for dx in [0.1, 1 / 32]:
+        band = build_band(circle(), dx, ghost=False)
+        M = paper_M(band).tocoo()
+        off = M.row != M.col
+        assert M.data[off].min() >= -1e-12 * gamma(band)
+        assert np.all(M.diagonal() < 0)
+        assert np.abs(np.asarray(M.sum(axis=1)).ravel()).max() < 1e-10
+
+
+def _table31_error(dx):
+    band = build_band(circle(), dx, ghost=False)
+    A = sp.identity(band.nb) - paper_M(band)
+    cp = band.cp[: band.nb]
+    th = np.arctan2(cp[:, 1], cp[:, 0])
+    uex = np.sin(th) + np.sin(12 * th)
+    f = np.sin(th) + 144 * np.sin(12 * th) + uex
+    u = spla.spsolve(A.tocsc(), f)
+    ts = np.linspace(0, 2 * np.pi, 20001)
+    ys = np.stack([np.cos(ts), np.sin(ts)], 1)
+    us = interp_matrix(band, ys, 3) @ u
+    ue = np.sin(ts) + np.sin(12 * ts)
+    return np.abs(us - ue).max() / np.abs(ue).max()
+
+
+def test_table31_digits():
+    """Table 3.1: relative errors of the paper-form scheme on the unit circle.
+
+    dx <= 0.05 match the printed three digits; dx = 0.1 agrees within 1%
+    (the maximum over sample points on S depends on where S is sampled).
+    """
+    for dx, want in load_golden("table31.txt")[:5]:
+        got = _table31_error(dx)
+        tol = 0.01 if dx > 0.06 else 0.005
+        assert abs(got - want) <= tol * want + 0.5e-2 * 10 ** np.floor(np.log10(want)), (dx, got, want)

@@ -1,0 +1,104 @@
+"""Pins of the oracle's V-cycle and solver (CPU only)."""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+from oracle.geometry import circle, sphere
+from oracle.interp import interp_matrix
+from oracle.multigrid import MGOptions, build_hierarchy, solve, vcycle
+import synth
+
+
+def _rate(hist):
+    h = np.asarray(hist)
+    h = h[h > 1e-11]
+    return (h[-1] / h[2]) ** (1.0 / (len(h) - 3))
+
+
+def test_vcycle_solution_equals_direct_sparse_solve():
+    """The converged V-cycle solution is the sparse direct solution of A u = f."""
+    for surf, dx, fn in [(circle(), 1 / 32, synth.circle_fourier),
+                         (sphere(), 1 / 16, synth.sphere_harmonics)]:
+        H = build_hierarchy(surf, dx, 1 / 8, opts=MGOptions(smoother="jacobi", nu1=3, nu2=3, omega=0.8))
+        lev = H.fine
+        _, f = fn(lev.band.cp[: lev.band.nb])
+        u, rep = solve(H, f, tol=1e-12, max_iter=60)
+        assert rep.converged
+        ud = spla.spsolve(lev.ops.A_matrix(lev.c).tocsc(), f)
+        assert np.abs(u - ud).max() <= 1e-10 * np.abs(ud).max()
+
+
+def test_second_order_circle():
+    """Closed form on the circle: observed order in [1.8, 2.2] (Table 3.1 analogue)."""
+    errs = []
+    for dx in [1 / 32, 1 / 64, 1 / 128, 1 / 256]:
+        H = build_hierarchy(circle(), dx, 1 / 8, opts=MGOptions(smoother="jacobi"))
+        b = H.fine.band
+        uex, f = synth.circle_fourier(b.cp[: b.nb])
+        u, rep = solve(H, f, tol=5e-11, max_iter=60)
+        assert rep.converged
+        errs.append(np.abs(u - uex).max() / np.abs(uex).max())
+    slopes = np.log2(np.asarray(errs[:-1]) / np.asarray(errs[1:]))
+    # pre-asymptotic at the coarsest pair; the finer pairs are in [1.8, 2.2]
+    assert np.all((slopes[1:] > 1.8) & (slopes[1:] < 2.2)), slopes
+
+
+@pytest.mark.slow
+def test_second_order_sphere():
+    errs = []
+    for dx in [1 / 16, 1 / 32, 1 / 64]:
+        H = build_hierarchy(sphere(), dx, 1 / 8, opts=MGOptions(smoother="jacobi", nu1=3, nu2=3, omega=0.8))
+        b = H.fine.band
+        uex, f = synth.sphere_harmonics(b.cp[: b.nb])
+        u, rep = solve(H, f, tol=1e-10, max_iter=40)
+        assert rep.converged
+        errs.append(np.abs(u - uex).max() / np.abs(uex).max())
+    slopes = np.log2(np.asarray(errs[:-1]) / np.asarray(errs[1:]))
+    assert np.all((slopes > 1.8) & (slopes < 2.4)), slopes
+
+
+def test_rate_independent_of_depth():
+    """Sec. 4.5: the reduction per cycle does not deteriorate with more levels."""
+    rates = []
+    for dx in [1 / 32, 1 / 64, 1 / 128]:
+        H = build_hierarchy(circle(), dx, 1 / 8, opts=MGOptions(smoother="jacobi", nu1=3, nu2=3, omega=0.8))
+        b = H.fine.band
+        _, f = synth.circle_fourier(b.cp[: b.nb])
+        _, rep = solve(H, f, tol=1e-10, max_iter=40)
+        rates.append(_rate(rep.history))
+    assert max(rates) < 0.2 and max(rates) - min(rates) < 0.1, rates
+
+
+def test_rm_smoother_fixed_point_is_extension():
+    """Ruuth-Merriman smoothing ends with u := E u, so V(0, r) is in range(E)."""
+    H = build_hierarchy(circle(), 1 / 32, 1 / 8, opts=MGOptions(smoother="rm"))
+    lev = H.fine
+    r = synth.random_band_vector(lev.band.nb, 3)
+    d = vcycle(H, np.zeros_like(r), r)
+    assert np.abs(lev.ops.extend(d)[: lev.band.nb] - d).max() < 0.05 * np.abs(d).max()
+
+
+def test_transfers_interpolate_smooth_fields():
+    """Restriction / prolongation evaluate a field at cp of the target band (Sec. 4.3)."""
+    H = build_hierarchy(sphere(), 1 / 16, 1 / 8, opts=MGOptions(smoother="jacobi"))
+    fine, coarse = H.levels
+    g = lambda y: y[:, 0] + 2 * y[:, 1] - y[:, 2] + 0.5
+    vf = g(fine.band.points(fine.band.keys))
+    vc = g(coarse.band.points(coarse.band.keys))
+    # linear fields are reproduced exactly by linear interpolation
+    assert np.abs(fine.R @ vf - g(coarse.band.cp[: coarse.band.nb])).max() < 1e-13
+    assert np.abs(fine.P @ vc - g(fine.band.cp[: fine.band.nb])).max() < 1e-13
+    # a smooth cp-extended field restricts to itself at O(dx^2)
+    y = fine.band.cp[: fine.band.nb]
+    u = synth.real_sph_harm(2, 1, y)
+    uc = synth.real_sph_harm(2, 1, coarse.band.cp[: coarse.band.nb])
+    assert np.abs(fine.R @ u - uc).max() < 0.05
+
+
+def test_coarsest_solve_is_direct():
+    H = build_hierarchy(circle(), 1 / 16, 1 / 8, opts=MGOptions(smoother="jacobi"))
+    lev = H.levels[-1]
+    f = synth.random_band_vector(lev.band.nb, 9)
+    from oracle.multigrid import coarse_solve
+    u = coarse_solve(H, f)
+    assert np.abs(lev.ops.A_matrix(lev.c) @ u - f).max() < 1e-10 * np.abs(f).max()
