@@ -1,0 +1,344 @@
+"""Benchmark: seconds to a 1e-10 relative residual on the unit sphere, dx = 1/256.
+
+One step = one complete solve of (1 - Lap_S) u = f on the unit sphere band at
+dx = 1/256 (6.79 M band points; f from 23 seeded spherical harmonics,
+l in {2, 3, 5}) from u = 0 until ||f - A u||_inf <= 1e-10 ||f||_inf, with the
+FP32 V-cycle preconditioning the FP64 outer loop (the headline form).  The
+plain FP64 V-cycle solve of the same system is timed beside it.
+
+Usage:  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl cpm|reference]
+For N > 1 it runs under torchrun, one independent replica per GPU (the solve
+does not shard); rank 0 prints one JSON line.
+
+``--impl reference`` times the CPU FP64 oracle (assembled sparse operators,
+CPU V-cycle) on a bounded sample of the same workload (the sphere at
+dx = 1/64 solved to 1e-10, scaled to dx = 1/256 by the band-size ratio).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+DX = 1.0 / 256
+METRIC = "s to 1e-10 rel residual, sphere Δx=1/256: FP32-IR/learned vs FP64; HBM GB/s"
+SAMPLE_DX = 1.0 / 64
+# FP64 flops of one extension evaluation per point: cubic weights (13 per axis)
+# and the separable 4x4x4 contraction (64 + 16 + 4 multiply-adds).
+EXTEND_FLOPS = 3 * 13 + 2 * (64 + 16 + 4)
+# FP32 extension bytes per point: key 8 + fractions 12 + u 4 + w 4.
+EXTEND32_BYTES = 28
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (profiling recipe table)
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except OSError:
+        return {"hbm_gbs": 6800.0, "fallback": True}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu: int):
+        self.gpu = gpu
+        self.rows = []
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if not self.rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in self.rows if len(r) > 2 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) > 2 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in self.rows:
+            for k, name in enumerate(names):
+                if len(r) > 5 + k and r[5 + k].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(self.rows)}
+
+
+def band_size(kind: str, inv_dx: int) -> int:
+    """|B| of the oracle's band, from tests/golden/band_sizes.txt (make_band_sizes.py)."""
+    with open(os.path.join(ROOT, "tests", "golden", "band_sizes.txt")) as fh:
+        for line in fh:
+            p = line.split()
+            if p and not line.startswith("#") and p[0] == kind and int(p[2]) == inv_dx:
+                return int(p[3])
+    raise KeyError((kind, inv_dx))
+
+
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Largest per-rank value (the slowest replica sets the job's time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+def oracle_sample(steps: int, warmup: int):
+    """Time the oracle (as it stands) on the bounded sample; seconds scaled to dx = 1/256."""
+    import numpy as np
+
+    import synth
+    from oracle.geometry import sphere
+    from oracle.multigrid import MGOptions, build_hierarchy, solve
+
+    t0 = time.perf_counter()
+    H = build_hierarchy(sphere(), SAMPLE_DX, 1 / 8, opts=MGOptions(smoother="jacobi", nu1=3, nu2=3, omega=0.8))
+    build_s = time.perf_counter() - t0
+    b = H.fine.band
+    _, f = synth.sphere_harmonics(b.cp[: b.nb])
+    scale = band_size("sphere", 256) / b.nb
+    times, iters = [], 0
+    for k in range(warmup + steps):
+        t = time.perf_counter()
+        u, rep = solve(H, f, tol=1e-10, max_iter=60)
+        dt = time.perf_counter() - t
+        if k >= warmup:
+            times.append(dt)
+            iters = rep.iters
+    per = statistics.median(times)
+    return {"value": per * scale, "sample_s": per, "scale": scale, "iters": iters,
+            "nb_sample": int(b.nb), "build_s": build_s, "times": times}
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    o = oracle_sample(args.steps, args.warmup)
+    sample = (f"oracle FP64 defect correction with its V-cycle (Jacobi nu=3/3, omega=0.8) on the "
+              f"unit sphere at dx=1/64 ({o['nb_sample']} band points) to 1e-10, median of "
+              f"{args.steps} solves = {o['sample_s']:.2f} s, scaled by the band-size ratio "
+              f"{o['scale']:.2f} to dx=1/256; assembly {o['build_s']:.1f} s excluded")
+    line = {"impl": "reference", "metric": METRIC, "value": o["value"], "unit": "s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": o["sample_s"] * 1e3, "higher_is_better": False, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "unit sphere dx=1/256 (bounded sample dx=1/64)", "tol": 1e-10},
+            "cpu_baseline": {"value": o["value"], "unit": "s", "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": o["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def run_cpm(args, world, rank, local):
+    import numpy as np
+    import torch
+
+    import paper_1307_4354_gb300 as pkg
+    import synth
+
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.build()
+    t0 = time.perf_counter()
+    band = pkg.Band("sphere", (), DX)
+    H = pkg.Hierarchy(band, coarsest_dx=1 / 8, nu1=3, nu2=3, omega=0.8)
+    setup_s = time.perf_counter() - t0
+    _, cp, _ = band.export()
+    _, f_np = synth.sphere_harmonics(cp[: band.nb])
+    nb = band.nb
+    f = torch.from_numpy(f_np).to(dev)
+    u = torch.zeros(nb, dtype=torch.float64, device=dev)
+    st = torch.cuda.current_stream()
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def solve(mode):
+        _, rep = H.solve(f, u, tol=1e-10, max_iter=200, mode=mode, zero_init=True,
+                         inner_cycles=args.inner)
+        assert rep["converged"], rep
+        return rep
+
+    # warm-up (also captures the CUDA graphs)
+    for _ in range(args.warmup):
+        solve("mixed")
+        solve("f64")
+    torch.cuda.synchronize()
+
+    # timed: mixed precision (headline)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = pkg.capi.cpm_kernel_launches()
+    with ClockSampler(local) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(st)
+        reps = [solve("mixed") for _ in range(args.steps)]
+        ev1.record(st)
+        torch.cuda.synchronize()
+        barrier()
+    mixed_ms = ev0.elapsed_time(ev1) / args.steps
+    launches = pkg.capi.cpm_kernel_launches() - launches0
+    mixed_ms = max_over_ranks(mixed_ms, world, dev)
+    iters_mixed = reps[-1]["iters"]
+
+    # plain FP64 solve (context)
+    k64 = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    ev0.record(st)
+    reps64 = [solve("f64") for _ in range(k64)]
+    ev1.record(st)
+    torch.cuda.synchronize()
+    f64_ms = ev0.elapsed_time(ev1) / k64
+
+    # end to end through the C ABI with host buffers
+    f_host = torch.from_numpy(f_np).pin_memory()
+    u_host = torch.empty(nb, dtype=torch.float64).pin_memory()
+    fd = torch.empty(nb, dtype=torch.float64, device=dev)
+    ud = torch.empty(nb, dtype=torch.float64, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ev0.record(st)
+    for _ in range(args.steps):
+        fd.copy_(f_host, non_blocking=True)
+        H.solve(fd, ud, tol=1e-10, max_iter=200, mode="mixed", zero_init=True,
+                inner_cycles=args.inner)
+        u_host.copy_(ud, non_blocking=True)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    e2e_ms = ev0.elapsed_time(ev1) / args.steps
+
+    # dominant kernel: FP64 extension over B+ (one launch = nB + nG points), CUDA events
+    # on the launching stream; and the FP32 extension for the memory roofline.
+    w64 = torch.empty(nb + band.ng, dtype=torch.float64, device=dev)
+    w32 = torch.empty(nb + band.ng, dtype=torch.float32, device=dev)
+    u32 = u.float()
+    for _ in range(3):
+        H.extend(u, with_ghost=True, out=w64)
+        H.extend(u32, with_ghost=True, out=w32)
+    reps_k = 20
+    torch.cuda.synchronize()
+    ev0.record(st)
+    for _ in range(reps_k):
+        H.extend(u, with_ghost=True, out=w64)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    ext64_ms = ev0.elapsed_time(ev1) / reps_k
+    ev0.record(st)
+    for _ in range(reps_k):
+        H.extend(u32, with_ghost=True, out=w32)
+    ev1.record(st)
+    torch.cuda.synchronize()
+    ext32_ms = ev0.elapsed_time(ev1) / reps_k
+    npl = nb + band.ng
+    ach64 = EXTEND_FLOPS * npl / (ext64_ms * 1e-3) / 1e12
+    ach32 = EXTEND32_BYTES * npl / (ext32_ms * 1e-3) / 1e9
+    pk = peaks()
+
+    if rank != 0:
+        return
+    cpu = oracle_sample(steps=1, warmup=0) if not args.no_cpu_baseline else None
+    nl = H.n_levels
+    sizes = [H.level_size(l) for l in range(nl)]
+    sweeps = 6
+    updates = sum(sizes[:-1]) * sweeps * iters_mixed
+    line = {
+        "metric": METRIC, "value": mixed_ms / 1e3, "unit": "s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed_ms,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"unit sphere dx=1/256 ({nb} band points, {band.ng} ghost), "
+                               "23 N(0,1) harmonics l in {2,3,5}, c=1, tol 1e-10, mixed FP32 V-cycle "
+                               "in FP64 defect correction",
+                   "levels": sizes, "smoother": "jacobi nu=3/3 omega=0.8", "transfers": "linear",
+                   "l2": "inputs larger than L2 (no flush)",
+                   "parallelism": f"replicas x{world}"},
+        "iters_mixed": iters_mixed, "fp64_s": f64_ms / 1e3, "iters_fp64": reps64[-1]["iters"],
+        "band_point_updates_per_s": updates / (mixed_ms * 1e-3),
+        "setup_s": setup_s,
+        "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": nb * 8,
+                "d2h_bytes_per_step": nb * 8},
+        "gpu_launches": int(launches),
+        "roofline": {"kernel": "k_extend<double,3> (FP64 extension over B+)", "bound": "alu",
+                     "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                     "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": None,
+                     "flops_per_point": EXTEND_FLOPS, "points": npl, "ms": ext64_ms},
+        "roofline_f32_extend": {"bound": "hbm", "achieved": ach32, "peak": pk.get("hbm_gbs"),
+                                "unit": "GB/s", "frac": ach32 / pk.get("hbm_gbs", 6800.0),
+                                "bytes_per_point": EXTEND32_BYTES, "ms": ext32_ms},
+        "clocks": clk.summary(),
+    }
+    if cpu:
+        line["cpu_baseline"] = {
+            "value": cpu["value"], "unit": "s", "cores": 1, "kind": "oracle",
+            "sample": f"oracle FP64 solve of the unit sphere at dx=1/64 ({cpu['nb_sample']} points) "
+                      f"to 1e-10 in {cpu['sample_s']:.2f} s, scaled x{cpu['scale']:.2f} to dx=1/256"}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="cpm", choices=["cpm", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--inner", type=int, default=1, help="FP32 V-cycles per outer iteration")
+    args = ap.parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_cpm(args, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,255 @@
+/*
+ * cpm.h -- C ABI of the GB300 (sm_103a) closest-point multigrid library.
+ *
+ * Solves the shifted surface Poisson equation (c - Lap_S) u = f on a closed
+ * curve or surface S (Chen & Macdonald, "The Closest Point Method and
+ * multigrid solvers for elliptic equations on surfaces", Sec. 2.1, Eq. 2.1)
+ * by the closest point method on a narrow band of a uniform Cartesian grid.
+ *
+ * The discrete system (Sec. 2.3 Eq. 2.10, Sec. 3.1, Remark 3.2) is
+ *
+ *     A u = f,   A = diag(c) - M,   M = diag(L) + (L - diag L) E,
+ *
+ * where L is the 2d+1-point Laplacian and E the degree-3 tensor-product
+ * barycentric Lagrange interpolation at each grid node's closest point
+ * (Sec. 3.1, Eq. 3.1).  The solver is the closest-point V-cycle of
+ * Algorithm 4.1 (Sec. 4) with weighted Jacobi smoothing (Eq. 4.1, Sec. 4.4),
+ * closest-point restriction and prolongation (Sec. 4.3) and a direct solve on
+ * the coarsest level, inside an outer defect-correction loop.
+ *
+ * Conventions for every entry point
+ * ---------------------------------
+ * - Status codes only; nothing throws across the ABI.  cpm_last_error()
+ *   returns a message for the last failing call of the calling thread.
+ * - Vectors are caller-owned DEVICE pointers of the stated length, in the
+ *   library's band order (bricks of 4x4x4 grid nodes in Morton order, nodes
+ *   inside a brick x-fastest); cpm_band_export gives the grid coordinates
+ *   of that order.  FP64 vectors are double*, FP32 vectors float*.
+ * - Handles own every device allocation they make; *_destroy frees them.
+ * - Calls are asynchronous on the given stream unless stated otherwise.
+ *   Passing 0 selects the legacy default stream.
+ * - Handles are not thread safe: one thread (or stream) at a time per handle.
+ */
+#ifndef CPM_H
+#define CPM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* cpm_stream; /* a cudaStream_t */
+
+typedef enum cpm_status {
+  CPM_OK = 0,
+  CPM_ERR_ARG = 1,          /* invalid argument, size or descriptor          */
+  CPM_ERR_OOM = 2,          /* device allocation failed                       */
+  CPM_ERR_CUDA = 3,         /* a CUDA runtime call failed                     */
+  CPM_ERR_REACH = 4,        /* band too wide for the surface: cp undefined on
+                               the ghost ring, or a stencil leaves the band  */
+  CPM_ERR_DIVERGED = 5,     /* residual grew 1e3x or became non-finite        */
+  CPM_ERR_NOT_CONVERGED = 6,/* max_iter reached above tolerance               */
+  CPM_ERR_TIMEOUT = 7,      /* a bounded device wait gave up                  */
+  CPM_ERR_CHECKED = 8,      /* a device-side bounds / consistency check failed */
+  CPM_ERR_SINGULAR = 9      /* coarsest-level matrix is singular              */
+} cpm_status;
+
+const char* cpm_status_str(cpm_status s);
+/* Message of the calling thread's last failing call ("" if none). */
+const char* cpm_last_error(void);
+
+/* ---------------------------------------------------------------- geometry */
+
+typedef enum cpm_surface_kind {
+  CPM_CIRCLE = 0,    /* d = 2, param[0] = radius R (centre at the origin)     */
+  CPM_SPHERE = 1,    /* d = 3, param[0] = radius R                             */
+  CPM_TORUS = 2,     /* d = 3, about the z axis: param[0] = R, param[1] = r    */
+  CPM_ELLIPSOID = 3  /* d = 3, semi-axes param[0..2]                           */
+} cpm_surface_kind;
+
+/* A closed surface with a closed-form or Newton closest point (Sec. 2.1). */
+typedef struct cpm_surface {
+  int32_t kind;      /* cpm_surface_kind */
+  int32_t pad_;
+  double param[8];
+} cpm_surface;
+
+/* Uniform grid x_i = lo + i dx, i = 0..n-1 on every axis (Sec. 3.1).
+ * n = 0 selects n = round(-2 lo / dx) + 1 (a grid symmetric about 0).
+ * lambda2 = 0 selects the tube radius^2 / dx^2 that makes the band contain
+ * every interpolation stencil and its difference stencils:
+ * (d-1)(p+1)^2/4 + (1+(p+1)/2)^2 with p = 3 (13 for d = 2, 17 for d = 3). */
+typedef struct cpm_grid {
+  double lo;
+  double dx;
+  int64_t n;
+  double lambda2;
+} cpm_grid;
+
+/* ---------------------------------------------------------------- band */
+
+typedef struct cpm_band_s* cpm_band;
+
+/*
+ * Build the band B = {x : |x - cp(x)|^2 <= lambda2 dx^2} (Sec. 3.1, the tube
+ * whose sizes match Table 4.1), its ghost ring G (Laplacian neighbours of B
+ * outside B) and the cubic stencil records of B+ = B with G, on the device.
+ * Membership is decided in FP64 with a fixed operation order (no fused
+ * multiply-add), so it is reproducible bit for bit.
+ * Errors: CPM_ERR_ARG for dx <= 0, an unknown kind or non-positive radii;
+ * CPM_ERR_REACH if cp is undefined on B+ or a stencil leaves B.
+ * Synchronous (returns after the band is built).
+ */
+cpm_status cpm_build_band(const cpm_surface* surface, const cpm_grid* grid,
+                          cpm_stream stream, cpm_band* out);
+
+/* |B| and |G|.  Synchronous, host outputs. */
+cpm_status cpm_band_info(cpm_band band, int64_t* n_band, int64_t* n_ghost);
+
+/*
+ * Copy out, for the n_band + n_ghost points of B+ in band order (B first,
+ * then G): grid coordinates ijk (int32 x d per point, may be NULL), closest
+ * points cp (double x d per point, may be NULL) and cubic stencil base nodes
+ * (int32 x d per point: floor((cp - lo)/dx) - 1, may be NULL).
+ * All outputs are HOST pointers.  Synchronous.
+ */
+cpm_status cpm_band_export(cpm_band band, int32_t* ijk, double* cp, int32_t* stencil_base);
+
+cpm_status cpm_band_destroy(cpm_band band);
+
+/* ---------------------------------------------------------------- hierarchy */
+
+typedef enum cpm_smoother {
+  CPM_SMOOTH_JACOBI = 0, /* weighted Jacobi on A (Eq. 4.1, Sec. 4.4)            */
+  CPM_SMOOTH_RM = 1      /* Ruuth-Merriman: Jacobi on cI - L, then u := E u
+                            (Eq. 4.2, Sec. 4.2)                                 */
+} cpm_smoother;
+
+typedef enum cpm_prec { CPM_F64 = 0, CPM_F32 = 1 } cpm_prec;
+
+typedef struct cpm_mg_opts {
+  double coarsest_dx;   /* spacing of the coarsest level (0: coarsen while
+                           (sqrt(lambda2)+1)*dx < reach and |B| > 64)           */
+  int32_t nu1, nu2;     /* pre / post smoothing sweeps (0: 3 and 3)             */
+  double omega;         /* Jacobi weight (0: 0.8)                               */
+  int32_t smoother;     /* cpm_smoother                                         */
+  int32_t transfer_deg; /* 1 (linear, Sec. 4.5) or 3 (0: 1)                     */
+  double c;             /* constant shift c > 0 (used when c_device is NULL)    */
+  const double* c_device; /* optional per-point c on the finest band (device,
+                             length n_band); coarse levels take c(cp) by
+                             linear interpolation from the finest band          */
+  int32_t residual_mode;  /* residual restricted by the Jacobi V-cycle:
+                             0: f - A (E u) (Sec. 4.4), 1: f - A u              */
+  int32_t coarse_sweeps;  /* coarsest level: 0 = direct solve (explicit FP64
+                             inverse) when it has <= 16384 points, else 40
+                             Jacobi sweeps; > 0 = that many Jacobi sweeps       */
+} cpm_mg_opts;
+
+typedef struct cpm_hier_s* cpm_hier;
+
+/*
+ * Build levels dx, 2dx, .., coarsest_dx (each with its own band, Sec. 4.3),
+ * the restriction and prolongation records, diag(A) on every level and the
+ * inverse of the coarsest-level matrix (FP64, for the direct solve of
+ * Algorithm 4.1 step 2).  The finest band is copied; `finest` may be
+ * destroyed afterwards.  Synchronous.
+ * Errors: CPM_ERR_ARG (bad options), CPM_ERR_REACH, CPM_ERR_SINGULAR.
+ */
+cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts,
+                               cpm_stream stream, cpm_hier* out);
+
+/* Number of levels and |B| of level l (host outputs, synchronous). */
+cpm_status cpm_hier_info(cpm_hier h, int32_t* n_levels, int32_t level, int64_t* n_band);
+
+/*
+ * Mu = M u on level `level` (0 = finest): w = E u on B+, then
+ * (Mu)_i = sum_{k in N(i)} (w_k - w_i)/dx^2 + gamma (w_i - u_i),
+ * gamma = 2d/dx^2 (spec operator, Sec. 2.3 Eq. 2.10).
+ * u, Mu: device vectors of length |B_level|, type per prec.
+ */
+cpm_status cpm_apply(cpm_hier h, int32_t level, int32_t prec, const void* u, void* Mu,
+                     cpm_stream stream);
+
+/*
+ * Closest-point extension w = E u on level `level` (Sec. 3.1 Eq. 3.1 with
+ * cubic tensor-product weights; the re-extension step of Eq. 4.2b): for every
+ * point x_i of B (and of the ghost ring G when with_ghost != 0), w_i is the
+ * degree-3 interpolant of u at cp(x_i) from the 4^d stencil nodes (all in B).
+ * u: device vector of length |B_level|; w: length |B_level| (+ |G_level| when
+ * with_ghost), B entries first.  Type per prec.
+ */
+cpm_status cpm_extend(cpm_hier h, int32_t level, int32_t prec, const void* u, void* w,
+                      int32_t with_ghost, cpm_stream stream);
+
+/*
+ * `sweeps` smoothing steps of the hierarchy's smoother on level `level` for
+ * A u = f, in place on u (Eq. 4.1 or Eq. 4.2).  f, u: device, |B_level|.
+ */
+cpm_status cpm_smooth(cpm_hier h, int32_t level, int32_t prec, const void* f, void* u,
+                      int32_t sweeps, cpm_stream stream);
+
+/*
+ * One V-cycle of Algorithm 4.1 from the finest level: u := V(u, f).
+ * prec = CPM_F64 runs every level in FP64; CPM_F32 runs them in FP32 with
+ * the coarsest solve in FP64.  f, u: device vectors of length |B_0|.
+ */
+cpm_status cpm_vcycle(cpm_hier h, int32_t prec, const void* f, void* u, cpm_stream stream);
+
+typedef enum cpm_solve_mode {
+  CPM_SOLVE_F64 = 0,   /* FP64 V-cycles in FP64 defect correction            */
+  CPM_SOLVE_MIXED = 1  /* FP32 V-cycle preconditioning an FP64 outer loop:
+                          r = f - A u in FP64, d = V32(r / s), u += s d      */
+} cpm_solve_mode;
+
+typedef struct cpm_solve_opts {
+  double tol;          /* stop when ||f - A u||_inf <= tol ||f||_inf (0: 1e-10) */
+  int32_t max_iter;    /* outer iterations (0: 100)                           */
+  int32_t mode;        /* cpm_solve_mode                                      */
+  int32_t use_graph;   /* capture the V-cycle in a CUDA graph (default 1 when
+                          opts is NULL; 0 = plain launches)                   */
+  int32_t zero_init;   /* 1: start from u = 0 (ignore u on entry)             */
+  int32_t inner_cycles;/* MIXED: FP32 V-cycles per outer iteration, each after
+                          the first starting from the previous correction
+                          (an FP32 inner defect correction; 0: 1)             */
+} cpm_solve_opts;
+
+#define CPM_MAX_HISTORY 256
+typedef struct cpm_solve_report {
+  int32_t iters;               /* outer iterations performed                  */
+  int32_t converged;           /* 1 if the tolerance was reached              */
+  double rel_residual;         /* final ||f - A u||_inf / ||f||_inf            */
+  double history[CPM_MAX_HISTORY]; /* relative residual before each iteration  */
+  double seconds;              /* wall time of the solve (host clock)         */
+} cpm_solve_report;
+
+/*
+ * Solve A u = f on the finest level.  f, u: FP64 device vectors of length
+ * |B_0|; u holds the initial guess unless zero_init.  The outer residual and
+ * the solution accumulator are FP64 in both modes.  Synchronous (reads one
+ * residual norm per outer iteration).  report may be NULL.
+ * Errors: CPM_ERR_NOT_CONVERGED, CPM_ERR_DIVERGED (u holds the last iterate).
+ */
+cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opts* opts,
+                     cpm_solve_report* report, cpm_stream stream);
+
+/*
+ * Relative residual ||f - A u||_inf / ||f||_inf and ||f - A u||_2 on the
+ * finest level in FP64 (host outputs).  Synchronous.
+ */
+cpm_status cpm_residual_norms(cpm_hier h, const double* f, const double* u, double* rel_inf,
+                              double* abs_l2, cpm_stream stream);
+
+/*
+ * Number of kernels this library has launched in the process so far (kernels
+ * inside replayed CUDA graphs included).  Host counter, no device work.
+ */
+int64_t cpm_kernel_launches(void);
+
+cpm_status cpm_hier_destroy(cpm_hier h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CPM_H */

@@ -28,7 +28,14 @@ bit with the CUDA path:
   t is the root, t > -min(a_i^2), of  sum_i a_i^2 x_i^2 / (a_i^2 + t)^2 = 1
   (the Lagrange condition for minimising |y - x|^2 on the surface).  The
   oracle finds t by plain bisection to the last bit (slow, obviously
-  convergent: the function is strictly decreasing on that interval).
+  convergent: the function is strictly decreasing on that interval), with
+      ax_i = |x_i| * a_i ;  bracket [-min a_i^2, sqrt((ax0^2+ax1^2)+ax2^2)+1e-300]
+      mid = 0.5*(lo+hi), stop when mid equals an end of the bracket
+      g_i = ax_i / (a_i^2 + mid) ;  F = ((g0*g0 + g1*g1) + g2*g2) - 1
+      F > 0 -> lo = mid, else hi = mid ;  t = 0.5*(lo+hi)
+      if F was never positive the node lies on the medial disk (the stationary
+      point is not the minimiser; the node is >= reach from S): dist2 = inf
+      cp_i = (a_i^2 * x_i) / (a_i^2 + t) ;  dist2 = (d0*d0 + d1*d1) + d2*d2
 """
 from __future__ import annotations
 
@@ -120,26 +127,35 @@ def _ellipsoid_t(X: np.ndarray, axes: np.ndarray, iters: int = 1100) -> np.ndarr
     amin2 = a2.min()
     ax = np.abs(X) * axes[None, :]
     lo = np.full(X.shape[0], -amin2)
-    hi = np.sqrt((ax * ax).sum(axis=1)) + 1e-300
+    hi = np.sqrt((ax[:, 0] * ax[:, 0] + ax[:, 1] * ax[:, 1]) + ax[:, 2] * ax[:, 2]) + 1e-300
+    moved = np.zeros(X.shape[0], dtype=bool)
     for _ in range(iters):
         mid = 0.5 * (lo + hi)
         if np.all((mid == lo) | (mid == hi)):
             break
-        g = ax / (a2[None, :] + mid[:, None])
-        F = (g * g).sum(axis=1) - 1.0
+        g0 = ax[:, 0] / (a2[0] + mid)
+        g1 = ax[:, 1] / (a2[1] + mid)
+        g2 = ax[:, 2] / (a2[2] + mid)
+        F = ((g0 * g0 + g1 * g1) + g2 * g2) - 1.0
         pos = F > 0
+        moved |= pos
         lo = np.where(pos, mid, lo)
         hi = np.where(pos, hi, mid)
-    return 0.5 * (lo + hi)
+    t = 0.5 * (lo + hi)
+    # F never positive: the root lies at or below -min a_i^2, x sits on the
+    # medial disk and the stationary point found is not the nearest point
+    # (such x are at least the reach away from S).
+    return np.where(moved, t, np.nan)
 
 
 def _ellipsoid(X: np.ndarray, axes):
     axes = np.asarray(axes, dtype=np.float64)
     t = _ellipsoid_t(X, axes)
     a2 = axes * axes
-    cp = a2[None, :] * X / (a2[None, :] + t[:, None])
+    cp = (a2[None, :] * X) / (a2[None, :] + t[:, None])
     diff = X - cp
     dist2 = (diff[:, 0] * diff[:, 0] + diff[:, 1] * diff[:, 1]) + diff[:, 2] * diff[:, 2]
+    dist2 = np.where(np.isnan(t), np.inf, dist2)
     return cp, dist2
 
 

@@ -19,13 +19,18 @@ Smoothers.
                with At = cI - L (band-restricted L), then u := E u.  The residual
                restricted in step 2 of Algorithm 4.1 is f - At u.
 * ``jacobi``   standard Jacobi on A (Eq. 4.1): u += omega diag(A)^-1 (f - A u);
-               the residual restricted in step 2 is f - A (E u) (Sec. 4.4).
+               the residual restricted in step 2 is f - A (E u) (Sec. 4.4,
+               ``residual="extended"``) or f - A u (``residual="plain"``).
 The paper uses omega = 1 with nu1 = nu2 = 3 (Sec. 4.5); the defaults here are
 omega = 2/3 and nu1 = nu2 = 2.
 
 V-cycle (Algorithm 4.1): nu1 smoothing steps, residual, restriction, either
 the direct coarsest solve or a recursive V-cycle from zero, prolongation and
 correction, nu2 smoothing steps.
+
+Coarsest level.  Direct LU solve (Algorithm 4.1 step 2); when that level is
+too large for a dense factorisation (``coarse_sweeps > 0``) a fixed number of
+weighted Jacobi sweeps on A from zero stands in for it.
 
 Outer loop.  Defect correction in float64:  r = f - A u  (A in the form of
 ``operators``), stop when ||r||_inf <= tol ||f||_inf, else u += V(0, r).
@@ -63,6 +68,8 @@ class MGOptions:
     smoother: str = "rm"              # "rm" | "jacobi"
     transfer_p: int = 1
     p: int = 3
+    residual: str = "extended"        # "extended": f - A(E u) (Sec. 4.4); "plain": f - A u
+    coarse_sweeps: int = 0            # > 0: coarsest level by Jacobi sweeps instead of LU
 
 
 @dataclass
@@ -103,7 +110,8 @@ def build_hierarchy(surface: Surface, dx: float, coarsest_dx: float, c=1.0,
         lev.diagA = lev.c - lev.ops.diag_M()
     hier = Hierarchy(levels, opts)
     last = levels[-1]
-    hier.lu = sla.lu_factor(last.ops.A_matrix(last.c).toarray())
+    if opts.coarse_sweeps == 0:
+        hier.lu = sla.lu_factor(last.ops.A_matrix(last.c).toarray())
     return hier
 
 
@@ -121,11 +129,20 @@ def transfer_residual(hier: Hierarchy, l: int, u: np.ndarray, f: np.ndarray) -> 
     lev, o = hier.levels[l], hier.opts
     if o.smoother == "rm":
         return f - lev.ops.apply_Atilde(u, lev.c)
+    if o.residual == "plain":
+        return f - lev.ops.apply_A(u, lev.c)
     wb = lev.ops.extend(u)[: lev.ops.nb]
     return f - lev.ops.apply_A(wb, lev.c)
 
 
 def coarse_solve(hier: Hierarchy, f: np.ndarray) -> np.ndarray:
+    o = hier.opts
+    if o.coarse_sweeps > 0:
+        last = hier.levels[-1]
+        u = np.zeros_like(f)
+        for _ in range(o.coarse_sweeps):
+            u = u + o.omega * (f - last.ops.apply_A(u, last.c)) / last.diagA
+        return u
     return sla.lu_solve(hier.lu, f)
 
 

@@ -1,0 +1,202 @@
+"""ctypes binding of the C ABI in ``include/cpm.h`` (argument marshalling only).
+
+Every function here has the name of the C entry point it calls and passes
+plain pointers and sizes; all computation happens in ``libcpm.so``.  Device
+vectors are passed as integer device addresses (``tensor.data_ptr()``) and
+streams as ``cudaStream_t`` integers (``torch.cuda.current_stream().cuda_stream``).
+A missing or unloadable library raises; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+from . import _build
+
+CPM_OK, CPM_ERR_ARG, CPM_ERR_OOM, CPM_ERR_CUDA, CPM_ERR_REACH = 0, 1, 2, 3, 4
+CPM_ERR_DIVERGED, CPM_ERR_NOT_CONVERGED, CPM_ERR_TIMEOUT, CPM_ERR_CHECKED, CPM_ERR_SINGULAR = 5, 6, 7, 8, 9
+CPM_CIRCLE, CPM_SPHERE, CPM_TORUS, CPM_ELLIPSOID = 0, 1, 2, 3
+CPM_SMOOTH_JACOBI, CPM_SMOOTH_RM = 0, 1
+CPM_F64, CPM_F32 = 0, 1
+CPM_RESID_EXTENDED, CPM_RESID_PLAIN = 0, 1
+CPM_SOLVE_F64, CPM_SOLVE_MIXED = 0, 1
+CPM_MAX_HISTORY = 256
+
+
+class cpm_surface(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("pad_", C.c_int32), ("param", C.c_double * 8)]
+
+
+class cpm_grid(C.Structure):
+    _fields_ = [("lo", C.c_double), ("dx", C.c_double), ("n", C.c_int64), ("lambda2", C.c_double)]
+
+
+class cpm_mg_opts(C.Structure):
+    _fields_ = [("coarsest_dx", C.c_double), ("nu1", C.c_int32), ("nu2", C.c_int32),
+                ("omega", C.c_double), ("smoother", C.c_int32), ("transfer_deg", C.c_int32),
+                ("c", C.c_double), ("c_device", C.c_void_p), ("residual_mode", C.c_int32),
+                ("coarse_sweeps", C.c_int32)]
+
+
+class cpm_solve_opts(C.Structure):
+    _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("mode", C.c_int32),
+                ("use_graph", C.c_int32), ("zero_init", C.c_int32), ("inner_cycles", C.c_int32)]
+
+
+class cpm_solve_report(C.Structure):
+    _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("rel_residual", C.c_double),
+                ("history", C.c_double * CPM_MAX_HISTORY), ("seconds", C.c_double)]
+
+
+class CpmError(RuntimeError):
+    def __init__(self, status: int, where: str, msg: str):
+        super().__init__(f"{where}: {msg} (status {status})")
+        self.status = status
+
+
+_lib = None
+
+# name -> (restype, argtypes)
+_PROTOS = {
+    "cpm_status_str": (C.c_char_p, [C.c_int]),
+    "cpm_last_error": (C.c_char_p, []),
+    "cpm_build_band": (C.c_int, [C.POINTER(cpm_surface), C.POINTER(cpm_grid), C.c_void_p,
+                                 C.POINTER(C.c_void_p)]),
+    "cpm_band_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+    "cpm_band_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cpm_band_destroy": (C.c_int, [C.c_void_p]),
+    "cpm_build_hierarchy": (C.c_int, [C.c_void_p, C.POINTER(cpm_mg_opts), C.c_void_p,
+                                      C.POINTER(C.c_void_p)]),
+    "cpm_hier_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int64)]),
+    "cpm_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cpm_extend": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                             C.c_void_p]),
+    "cpm_kernel_launches": (C.c_int64, []),
+    "cpm_smooth": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                             C.c_void_p]),
+    "cpm_vcycle": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cpm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(cpm_solve_opts),
+                            C.POINTER(cpm_solve_report), C.c_void_p]),
+    "cpm_residual_norms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
+                                     C.POINTER(C.c_double), C.c_void_p]),
+    "cpm_hier_destroy": (C.c_int, [C.c_void_p]),
+}
+
+
+def exported_names():
+    """Entry points declared in include/cpm.h and bound here."""
+    return sorted(_PROTOS)
+
+
+def lib(path: str | None = None):
+    """Load libcpm.so (raises if it was not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or _build.LIB
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_1307_4354_gb300._build.build()")
+    L = C.CDLL(path)
+    for name, (res, args) in _PROTOS.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(status: int, where: str):
+    if status != CPM_OK:
+        L = lib()
+        raise CpmError(status, where, (L.cpm_last_error() or b"").decode() or
+                       L.cpm_status_str(status).decode())
+
+
+def cpm_status_str(status: int) -> str:
+    return lib().cpm_status_str(status).decode()
+
+
+def cpm_last_error() -> str:
+    return lib().cpm_last_error().decode()
+
+
+def cpm_build_band(surface: cpm_surface, grid: cpm_grid, stream: int = 0) -> int:
+    out = C.c_void_p()
+    _check(lib().cpm_build_band(C.byref(surface), C.byref(grid), C.c_void_p(stream), C.byref(out)),
+           "cpm_build_band")
+    return out.value
+
+
+def cpm_band_info(band: int):
+    nb, ng = C.c_int64(), C.c_int64()
+    _check(lib().cpm_band_info(C.c_void_p(band), C.byref(nb), C.byref(ng)), "cpm_band_info")
+    return nb.value, ng.value
+
+
+def cpm_band_export(band: int, ijk_ptr: int | None, cp_ptr: int | None, base_ptr: int | None):
+    _check(lib().cpm_band_export(C.c_void_p(band), C.c_void_p(ijk_ptr), C.c_void_p(cp_ptr),
+                                 C.c_void_p(base_ptr)), "cpm_band_export")
+
+
+def cpm_band_destroy(band: int):
+    _check(lib().cpm_band_destroy(C.c_void_p(band)), "cpm_band_destroy")
+
+
+def cpm_build_hierarchy(band: int, opts: cpm_mg_opts, stream: int = 0) -> int:
+    out = C.c_void_p()
+    _check(lib().cpm_build_hierarchy(C.c_void_p(band), C.byref(opts), C.c_void_p(stream),
+                                     C.byref(out)), "cpm_build_hierarchy")
+    return out.value
+
+
+def cpm_hier_info(h: int, level: int = 0):
+    nl, nb = C.c_int32(), C.c_int64()
+    _check(lib().cpm_hier_info(C.c_void_p(h), C.byref(nl), level, C.byref(nb)), "cpm_hier_info")
+    return nl.value, nb.value
+
+
+def cpm_apply(h: int, level: int, prec: int, u_ptr: int, Mu_ptr: int, stream: int = 0):
+    _check(lib().cpm_apply(C.c_void_p(h), level, prec, C.c_void_p(u_ptr), C.c_void_p(Mu_ptr),
+                           C.c_void_p(stream)), "cpm_apply")
+
+
+def cpm_extend(h: int, level: int, prec: int, u_ptr: int, w_ptr: int, with_ghost: bool,
+               stream: int = 0):
+    _check(lib().cpm_extend(C.c_void_p(h), level, prec, C.c_void_p(u_ptr), C.c_void_p(w_ptr),
+                            int(with_ghost), C.c_void_p(stream)), "cpm_extend")
+
+
+def cpm_kernel_launches() -> int:
+    return int(lib().cpm_kernel_launches())
+
+
+def cpm_smooth(h: int, level: int, prec: int, f_ptr: int, u_ptr: int, sweeps: int, stream: int = 0):
+    _check(lib().cpm_smooth(C.c_void_p(h), level, prec, C.c_void_p(f_ptr), C.c_void_p(u_ptr), sweeps,
+                            C.c_void_p(stream)), "cpm_smooth")
+
+
+def cpm_vcycle(h: int, prec: int, f_ptr: int, u_ptr: int, stream: int = 0):
+    _check(lib().cpm_vcycle(C.c_void_p(h), prec, C.c_void_p(f_ptr), C.c_void_p(u_ptr),
+                            C.c_void_p(stream)), "cpm_vcycle")
+
+
+def cpm_solve(h: int, f_ptr: int, u_ptr: int, opts: cpm_solve_opts, stream: int = 0,
+              raise_on_fail: bool = True) -> tuple[int, cpm_solve_report]:
+    rep = cpm_solve_report()
+    st = lib().cpm_solve(C.c_void_p(h), C.c_void_p(f_ptr), C.c_void_p(u_ptr), C.byref(opts),
+                         C.byref(rep), C.c_void_p(stream))
+    if raise_on_fail:
+        _check(st, "cpm_solve")
+    return st, rep
+
+
+def cpm_residual_norms(h: int, f_ptr: int, u_ptr: int, stream: int = 0):
+    rel, l2 = C.c_double(), C.c_double()
+    _check(lib().cpm_residual_norms(C.c_void_p(h), C.c_void_p(f_ptr), C.c_void_p(u_ptr),
+                                    C.byref(rel), C.byref(l2), C.c_void_p(stream)),
+           "cpm_residual_norms")
+    return rel.value, l2.value
+
+
+def cpm_hier_destroy(h: int):
+    _check(lib().cpm_hier_destroy(C.c_void_p(h)), "cpm_hier_destroy")

@@ -1,0 +1,763 @@
+// Multigrid hierarchy, V-cycle (Algorithm 4.1), outer solve loop and the
+// C ABI entry points declared in include/cpm.h.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <vector>
+
+#include "ops.cuh"
+
+namespace cpm {
+
+thread_local std::string g_last_error;
+int64_t launches_total();
+void set_last_error(const std::string& msg) { g_last_error = msg; }
+
+static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ----------------------------------------------------------------- transfer records
+// For each target point (its cp), the base node floor((cp - lo)/dx_src) of the
+// linear stencil in the source grid and the fractions; every stencil node
+// must be a band node of the source level.
+__global__ void k_transfer_records(const double* cp, int64_t cp_stride, int32_t n, int dim,
+                                   double lo, double dx, BrickView src, uint64_t* base,
+                                   double* fr64, float* fr32, int32_t* err) {
+  const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  int b[3] = {0, 0, 0};
+  for (int a = 0; a < dim; ++a) {
+    const double t = __ddiv_rn(__dadd_rn(cp[a * cp_stride + j], -lo), dx);
+    const double fl = floor(t);
+    const double s = __dadd_rn(t, -fl);
+    b[a] = (int)fl;
+    fr64[(int64_t)a * n + j] = s;
+    fr32[(int64_t)a * n + j] = (float)s;
+  }
+  base[j] = (uint64_t)(uint32_t)b[0] | ((uint64_t)(uint32_t)b[1] << 16) | ((uint64_t)(uint32_t)b[2] << 32);
+  for (int c = 0; c < (dim == 3 ? 2 : 1); ++c)
+    for (int bb = 0; bb < 2; ++bb)
+      for (int a = 0; a < 2; ++a)
+        if (band_index(src, b[0] + a, b[1] + bb, b[2] + c) < 0) atomicOr(err, 4);
+}
+
+// dA = c - diag(M) in FP64 and FP32.
+__global__ void k_diag_A(const double* diagM, const double* cvec, double cval, double* dA64,
+                         float* dA32, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double v = (cvec ? cvec[i] : cval) - diagM[i];
+  dA64[i] = v;
+  dA32[i] = (float)v;
+}
+
+struct Transfer {
+  DBuf<uint64_t> base;
+  DBuf<double> fr64;
+  DBuf<float> fr32;
+  int32_t n = 0;
+};
+
+template <typename T>
+struct Work {
+  DBuf<T> u, f, r, w, tmp;
+  void alloc(int64_t nB, int64_t nplus) {
+    u.alloc(nB);
+    f.alloc(nB);
+    r.alloc(nB);
+    w.alloc(nplus);
+    tmp.alloc(nB);
+  }
+};
+
+struct HLevel {
+  std::unique_ptr<Level> lev;
+  DBuf<double> c64;   // per-point c (empty: scalar)
+  DBuf<float> c32;
+  DBuf<double> dA64;  // c - diag(M)
+  DBuf<float> dA32;
+  Transfer R;  // restriction: targets = B of level l+1, source = this level
+  Transfer P;  // prolongation: targets = B of this level, source = level l+1
+  Work<double> w64;
+  Work<float> w32;
+
+  template <typename T>
+  LevelView<T> view() const;
+  template <typename T>
+  Work<T>& work();
+  template <typename T>
+  const T* cvec() const;
+  template <typename T>
+  const T* dA() const;
+};
+
+template <>
+LevelView<double> HLevel::view<double>() const {
+  LevelView<double> v;
+  v.bv = lev->view();
+  v.key = lev->key.get();
+  v.fr = lev->fr64.get();
+  v.nplus = lev->nplus();
+  v.nB = lev->nB;
+  v.dim = lev->dim;
+  v.inv_h2 = 1.0 / (lev->dx * lev->dx);
+  v.gamma = 2.0 * lev->dim / (lev->dx * lev->dx);
+  return v;
+}
+template <>
+LevelView<float> HLevel::view<float>() const {
+  LevelView<float> v;
+  v.bv = lev->view();
+  v.key = lev->key.get();
+  v.fr = lev->fr32.get();
+  v.nplus = lev->nplus();
+  v.nB = lev->nB;
+  v.dim = lev->dim;
+  v.inv_h2 = (float)(1.0 / (lev->dx * lev->dx));
+  v.gamma = (float)(2.0 * lev->dim / (lev->dx * lev->dx));
+  return v;
+}
+template <> Work<double>& HLevel::work<double>() { return w64; }
+template <> Work<float>& HLevel::work<float>() { return w32; }
+template <> const double* HLevel::cvec<double>() const { return c64.get(); }
+template <> const float* HLevel::cvec<float>() const { return c32.get(); }
+template <> const double* HLevel::dA<double>() const { return dA64.get(); }
+template <> const float* HLevel::dA<float>() const { return dA32.get(); }
+
+template <typename T>
+static TransferView<T> tview(const Transfer& t, const Level& src, int dim);
+template <>
+TransferView<double> tview<double>(const Transfer& t, const Level& src, int dim) {
+  return TransferView<double>{t.base.get(), t.fr64.get(), t.n, src.view(), dim};
+}
+template <>
+TransferView<float> tview<float>(const Transfer& t, const Level& src, int dim) {
+  return TransferView<float>{t.base.get(), t.fr32.get(), t.n, src.view(), dim};
+}
+
+}  // namespace cpm
+
+using namespace cpm;
+
+struct cpm_hier_s {
+  cpm_surface surface;
+  cpm_mg_opts opts;
+  double c = 1.0;
+  std::vector<HLevel> L;
+  DBuf<double> Ainv;
+  int32_t nc = 0;
+  int32_t coarse_sweeps = 0;  // 0: direct solve with Ainv
+  DBuf<double> part;   // norm partials (2 per block)
+  int part_blocks = 0;
+  DBuf<double> norms;  // [max, sumsq, 1/max]
+  DBuf<double> normf;  // norms of f
+  DBuf<double> u_own, f_own, r64, d64;
+  DBuf<float> r32, d32;
+  cudaStream_t hs = nullptr;
+  cudaEvent_t ev = nullptr;
+  cudaGraphExec_t graph[2] = {nullptr, nullptr};
+  int64_t graph_kernels[2] = {0, 0};
+  int32_t graph_inner[2] = {0, 0};
+  double* pinned = nullptr;
+  ~cpm_hier_s() {
+    for (auto& g : graph)
+      if (g) cudaGraphExecDestroy(g);
+    if (ev) cudaEventDestroy(ev);
+    if (hs) cudaStreamDestroy(hs);
+    if (pinned) cudaFreeHost(pinned);
+  }
+};
+
+namespace cpm {
+
+// ----------------------------------------------------------------- level ops
+template <typename T>
+static void smooth(cpm_hier_s* H, int l, const T* f, T* u, int sweeps, cudaStream_t st) {
+  HLevel& lv = H->L[l];
+  const LevelView<T> v = lv.view<T>();
+  Work<T>& w = lv.work<T>();
+  const T omega = (T)H->opts.omega;
+  const T cval = (T)H->c;
+  for (int s = 0; s < sweeps; ++s) {
+    if (H->opts.smoother == CPM_SMOOTH_RM) {
+      launch_rm_jacobi<T>(v, u, f, lv.cvec<T>(), cval, omega, w.tmp.get(), st);
+      launch_extend<T>(v, w.tmp.get(), u, v.nB, st);
+    } else {
+      launch_extend<T>(v, u, w.w.get(), (int32_t)v.nplus, st);
+      launch_lap<T>(v, LAP_JACOBI, u, w.w.get(), f, lv.cvec<T>(), cval, lv.dA<T>(), omega, nullptr,
+                    u, nullptr, 0, st);
+    }
+  }
+}
+
+// r = f - A u (Jacobi smoother) or f - (cI - L) u (Ruuth-Merriman, Algorithm 4.1 step 2).
+template <typename T>
+static void transfer_residual(cpm_hier_s* H, int l, const T* f, const T* u, T* r, cudaStream_t st) {
+  HLevel& lv = H->L[l];
+  const LevelView<T> v = lv.view<T>();
+  Work<T>& w = lv.work<T>();
+  if (H->opts.smoother == CPM_SMOOTH_RM) {
+    launch_rm_resid<T>(v, u, f, lv.cvec<T>(), (T)H->c, r, st);
+  } else if (H->opts.residual_mode == 1) {
+    launch_extend<T>(v, u, w.w.get(), (int32_t)v.nplus, st);
+    launch_lap<T>(v, LAP_RESID, u, w.w.get(), f, lv.cvec<T>(), (T)H->c, nullptr, T(0), r, nullptr,
+                  nullptr, 0, st);
+  } else {
+    // f - A (E u): first E u on B, then the residual of that re-extended iterate
+    launch_extend<T>(v, u, w.tmp.get(), v.nB, st);
+    launch_extend<T>(v, w.tmp.get(), w.w.get(), (int32_t)v.nplus, st);
+    launch_lap<T>(v, LAP_RESID, w.tmp.get(), w.w.get(), f, lv.cvec<T>(), (T)H->c, nullptr, T(0), r,
+                  nullptr, nullptr, 0, st);
+  }
+}
+
+// Coarsest level: explicit FP64 inverse, or weighted Jacobi sweeps from zero.
+template <typename T>
+static void coarse_solve(cpm_hier_s* H, const T* f, T* u, cudaStream_t st) {
+  const int l = (int)H->L.size() - 1;
+  if (H->coarse_sweeps == 0) {
+    launch_coarse_gemv<T>(H->Ainv.get(), f, u, H->nc, st);
+    return;
+  }
+  CPM_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(T) * H->L[l].lev->nB, st));
+  HLevel& lv = H->L[l];
+  const LevelView<T> v = lv.view<T>();
+  Work<T>& w = lv.work<T>();
+  for (int s = 0; s < H->coarse_sweeps; ++s) {
+    launch_extend<T>(v, u, w.w.get(), (int32_t)v.nplus, st);
+    launch_lap<T>(v, LAP_JACOBI, u, w.w.get(), f, lv.cvec<T>(), (T)H->c, lv.dA<T>(),
+                  (T)H->opts.omega, nullptr, u, nullptr, 0, st);
+  }
+}
+
+template <typename T>
+static void vcycle_level(cpm_hier_s* H, int l, const T* f, T* u, cudaStream_t st) {
+  const int nl = (int)H->L.size();
+  if (l == nl - 1) {
+    coarse_solve<T>(H, f, u, st);
+    return;
+  }
+  HLevel& lv = H->L[l];
+  HLevel& cv = H->L[l + 1];
+  Work<T>& w = lv.work<T>();
+  Work<T>& cw = cv.work<T>();
+  smooth<T>(H, l, f, u, H->opts.nu1, st);
+  transfer_residual<T>(H, l, f, u, w.r.get(), st);
+  launch_transfer<T>(tview<T>(lv.R, *lv.lev, lv.lev->dim), w.r.get(), cw.f.get(), false, st);
+  if (l + 1 < nl - 1)
+    CPM_CUDA_TRY(cudaMemsetAsync(cw.u.get(), 0, sizeof(T) * cv.lev->nB, st));
+  vcycle_level<T>(H, l + 1, cw.f.get(), cw.u.get(), st);
+  launch_transfer<T>(tview<T>(lv.P, *cv.lev, lv.lev->dim), cw.u.get(), u, true, st);
+  smooth<T>(H, l, f, u, H->opts.nu2, st);
+}
+
+// FP64 outer residual r = f - A u on the finest level with norms into H->norms.
+static void outer_residual(cpm_hier_s* H, const double* f, const double* u, double* r, cudaStream_t st) {
+  HLevel& lv = H->L[0];
+  const LevelView<double> v = lv.view<double>();
+  launch_extend<double>(v, u, lv.w64.w.get(), (int32_t)v.nplus, st);
+  launch_lap<double>(v, LAP_RESID, u, lv.w64.w.get(), f, lv.c64.get(), H->c, nullptr, 0.0, r, nullptr,
+                     H->part.get(), H->part_blocks, st);
+  launch_norm_final(H->part.get(), nblk(v.nB, 256), H->norms.get(), st);
+}
+
+// One outer iteration after the residual: u += V(0, r), then the new residual.
+static void outer_step(cpm_hier_s* H, int mode, int inner, cudaStream_t st) {
+  const int64_t nB = H->L[0].lev->nB;
+  if (mode == CPM_SOLVE_F64) {
+    CPM_CUDA_TRY(cudaMemsetAsync(H->d64.get(), 0, sizeof(double) * nB, st));
+    vcycle_level<double>(H, 0, H->r64.get(), H->d64.get(), st);
+    launch_axpy64(H->u_own.get(), H->d64.get(), nB, st);
+  } else {
+    launch_scale_to_f32(H->r64.get(), H->norms.get(), H->r32.get(), nB, st);
+    CPM_CUDA_TRY(cudaMemsetAsync(H->d32.get(), 0, sizeof(float) * nB, st));
+    for (int j = 0; j < inner; ++j) vcycle_level<float>(H, 0, H->r32.get(), H->d32.get(), st);
+    launch_axpy_scaled(H->u_own.get(), H->d32.get(), H->norms.get(), nB, st);
+  }
+  outer_residual(H, H->f_own.get(), H->u_own.get(), H->r64.get(), st);
+}
+
+}  // namespace cpm
+
+// ----------------------------------------------------------------- C ABI
+#define CPM_API_BEGIN try {
+#define CPM_API_END                                                    \
+  }                                                                    \
+  catch (const cpm::Error& e) {                                        \
+    cpm::set_last_error(e.msg);                                        \
+    return e.status;                                                   \
+  }                                                                    \
+  catch (const std::bad_alloc&) {                                      \
+    cpm::set_last_error("host allocation failed");                     \
+    return CPM_ERR_OOM;                                                \
+  }                                                                    \
+  catch (...) {                                                        \
+    cpm::set_last_error("unexpected exception");                       \
+    return CPM_ERR_CUDA;                                               \
+  }                                                                    \
+  return CPM_OK;
+
+extern "C" {
+
+const char* cpm_status_str(cpm_status s) {
+  switch (s) {
+    case CPM_OK: return "ok";
+    case CPM_ERR_ARG: return "invalid argument";
+    case CPM_ERR_OOM: return "out of device memory";
+    case CPM_ERR_CUDA: return "CUDA error";
+    case CPM_ERR_REACH: return "band wider than the closest-point reach";
+    case CPM_ERR_DIVERGED: return "diverged";
+    case CPM_ERR_NOT_CONVERGED: return "not converged";
+    case CPM_ERR_TIMEOUT: return "timeout";
+    case CPM_ERR_CHECKED: return "device check failed";
+    case CPM_ERR_SINGULAR: return "singular coarsest matrix";
+  }
+  return "unknown status";
+}
+
+const char* cpm_last_error(void) { return cpm::g_last_error.c_str(); }
+
+static void check_surface(const cpm_surface* s) {
+  CPM_CHECK(s != nullptr, CPM_ERR_ARG, "surface is NULL");
+  CPM_CHECK(s->kind >= CPM_CIRCLE && s->kind <= CPM_ELLIPSOID, CPM_ERR_ARG, "unknown surface kind");
+  const int np = s->kind == CPM_TORUS ? 2 : (s->kind == CPM_ELLIPSOID ? 3 : 1);
+  for (int i = 0; i < np; ++i)
+    CPM_CHECK(s->param[i] > 0 && std::isfinite(s->param[i]), CPM_ERR_ARG,
+              "surface parameters must be positive");
+  if (s->kind == CPM_TORUS)
+    CPM_CHECK(s->param[1] < s->param[0], CPM_ERR_ARG, "torus needs r < R");
+}
+
+static double default_lambda2(int dim) { return dim == 3 ? 17.0 : 13.0; }
+
+static int grid_n(const cpm_grid* g) {
+  if (g->n > 0) return (int)g->n;
+  return (int)std::llround(-2.0 * g->lo / g->dx) + 1;
+}
+
+cpm_status cpm_build_band(const cpm_surface* surface, const cpm_grid* grid, cpm_stream stream,
+                          cpm_band* out) {
+  CPM_API_BEGIN
+  CPM_CHECK(out != nullptr && grid != nullptr, CPM_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  check_surface(surface);
+  CPM_CHECK(grid->dx > 0 && std::isfinite(grid->dx), CPM_ERR_ARG, "dx must be positive");
+  CPM_CHECK(grid->lo < 0 && std::isfinite(grid->lo), CPM_ERR_ARG, "lo must be negative");
+  const int dim = surface_dim(*surface);
+  const double lam2 = grid->lambda2 > 0 ? grid->lambda2 : default_lambda2(dim);
+  std::unique_ptr<cpm_band_s> b(new cpm_band_s);
+  b->surface = *surface;
+  build_level(*surface, grid->lo, grid->dx, grid_n(grid), lam2, (cudaStream_t)stream, b->lev);
+  *out = b.release();
+  CPM_API_END
+}
+
+cpm_status cpm_band_info(cpm_band band, int64_t* n_band, int64_t* n_ghost) {
+  CPM_API_BEGIN
+  CPM_CHECK(band != nullptr, CPM_ERR_ARG, "band is NULL");
+  if (n_band) *n_band = band->lev.nB;
+  if (n_ghost) *n_ghost = band->lev.nG;
+  CPM_API_END
+}
+
+static void export_level(const Level& L, int32_t* ijk, double* cp, int32_t* base) {
+  const int64_t np = L.nplus();
+  const int d = L.dim;
+  std::vector<uint64_t> key(np);
+  CPM_CUDA_TRY(cudaDeviceSynchronize());
+  CPM_CUDA_TRY(cudaMemcpy(key.data(), L.key.get(), np * sizeof(uint64_t), cudaMemcpyDeviceToHost));
+  if (cp) {
+    std::vector<double> c((size_t)d * np);
+    CPM_CUDA_TRY(cudaMemcpy(c.data(), L.cp.get(), c.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < np; ++i)
+      for (int a = 0; a < d; ++a) cp[i * d + a] = c[(size_t)a * np + i];
+  }
+  for (int64_t i = 0; i < np; ++i) {
+    const uint64_t k = key[i];
+    const int own[3] = {key_x(k), key_y(k), key_z(k)};
+    const int off[3] = {key_ox(k), key_oy(k), key_oz(k)};
+    for (int a = 0; a < d; ++a) {
+      if (ijk) ijk[i * d + a] = own[a];
+      if (base) base[i * d + a] = own[a] + off[a];
+    }
+  }
+}
+
+cpm_status cpm_band_export(cpm_band band, int32_t* ijk, double* cp, int32_t* stencil_base) {
+  CPM_API_BEGIN
+  CPM_CHECK(band != nullptr, CPM_ERR_ARG, "band is NULL");
+  export_level(band->lev, ijk, cp, stencil_base);
+  CPM_API_END
+}
+
+cpm_status cpm_band_destroy(cpm_band band) {
+  CPM_API_BEGIN
+  delete band;
+  CPM_API_END
+}
+
+// Copy a level (device to device) so the hierarchy owns its finest band.
+static void copy_level(const Level& a, Level& b, cudaStream_t st) {
+  b.dim = a.dim; b.lo = a.lo; b.dx = a.dx; b.lambda2 = a.lambda2; b.n = a.n;
+  b.nbx = a.nbx; b.nby = a.nby; b.nbz = a.nbz; b.nbricks = a.nbricks; b.nB = a.nB; b.nG = a.nG;
+  auto cp = [&](auto& dst, const auto& src) {
+    dst.alloc(src.n);
+    if (src.n)
+      CPM_CUDA_TRY(cudaMemcpyAsync(dst.get(), src.get(), src.n * sizeof(*src.get()),
+                                   cudaMemcpyDeviceToDevice, st));
+  };
+  cp(b.map, a.map); cp(b.bmask, a.bmask); cp(b.gmask, a.gmask); cp(b.bstart, a.bstart);
+  cp(b.gstart, a.gstart); cp(b.bcoord, a.bcoord); cp(b.key, a.key); cp(b.cp, a.cp);
+  cp(b.fr64, a.fr64); cp(b.fr32, a.fr32);
+}
+
+static void build_transfer(const Level& target, const Level& src, Transfer& t, cudaStream_t st,
+                           int32_t* err) {
+  t.n = target.nB;
+  t.base.alloc(t.n);
+  t.fr64.alloc((size_t)target.dim * t.n);
+  t.fr32.alloc((size_t)target.dim * t.n);
+  k_transfer_records<<<nblk(t.n, 256), 256, 0, st>>>(target.cp.get(), target.nplus(), t.n, target.dim,
+                                                     src.lo, src.dx, src.view(), t.base.get(),
+                                                     t.fr64.get(), t.fr32.get(), err);
+  CPM_CUDA_TRY(cudaGetLastError());
+}
+
+cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_stream stream,
+                               cpm_hier* out) {
+  CPM_API_BEGIN
+  CPM_CHECK(finest != nullptr && out != nullptr, CPM_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  cudaStream_t st = (cudaStream_t)stream;
+  cpm_mg_opts o{};
+  if (opts_in) o = *opts_in;
+  if (o.nu1 <= 0 && o.nu2 <= 0) { o.nu1 = 3; o.nu2 = 3; }
+  if (o.omega <= 0) o.omega = 0.8;
+  if (o.transfer_deg == 0) o.transfer_deg = 1;
+  CPM_CHECK(o.transfer_deg == 1, CPM_ERR_ARG, "only linear transfers (degree 1) are implemented");
+  CPM_CHECK(o.smoother == CPM_SMOOTH_JACOBI || o.smoother == CPM_SMOOTH_RM, CPM_ERR_ARG,
+            "unknown smoother");
+  CPM_CHECK(o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 <= 64, CPM_ERR_ARG, "bad sweep counts");
+  if (!(o.c > 0)) o.c = 1.0;
+  CPM_CHECK(std::isfinite(o.c), CPM_ERR_ARG, "c must be finite");
+  std::unique_ptr<cpm_hier_s> H(new cpm_hier_s);
+  H->surface = finest->surface;
+  H->opts = o;
+  H->c = o.c;
+  const Level& f0 = finest->lev;
+  const double reach = surface_reach(finest->surface);
+  const double lam = std::sqrt(f0.lambda2);
+
+  // levels
+  H->L.emplace_back();
+  H->L[0].lev.reset(new Level);
+  copy_level(f0, *H->L[0].lev, st);
+  double dx = f0.dx;
+  for (;;) {
+    const double next = 2.0 * dx;
+    const Level& cur = *H->L.back().lev;
+    bool more;
+    if (o.coarsest_dx > 0) {
+      more = next <= o.coarsest_dx * (1 + 1e-12);
+      CPM_CHECK(!more || (lam + 1.0) * next < reach, CPM_ERR_REACH,
+                "coarsest_dx too coarse for the surface reach");
+    } else {
+      more = (lam + 1.0) * next < reach && cur.nB > 64;
+    }
+    if (!more) break;
+    const int n_next = (int)std::llround(-2.0 * f0.lo / next) + 1;
+    CPM_CHECK(std::fabs((n_next - 1) * next + 2.0 * f0.lo) < 1e-9 * next, CPM_ERR_ARG,
+              "coarse grid does not nest (lo must be a multiple of the coarse spacing)");
+    H->L.emplace_back();
+    H->L.back().lev.reset(new Level);
+    build_level(finest->surface, f0.lo, next, n_next, f0.lambda2, st, *H->L.back().lev);
+    dx = next;
+  }
+  const int nl = (int)H->L.size();
+  const Level& cl = *H->L[nl - 1].lev;
+  CPM_CHECK(o.coarse_sweeps >= 0 && o.coarse_sweeps <= 10000, CPM_ERR_ARG, "bad coarse_sweeps");
+  H->coarse_sweeps = o.coarse_sweeps > 0 ? o.coarse_sweeps : (cl.nB <= 16384 ? 0 : 40);
+  CPM_CHECK(o.residual_mode == 0 || o.residual_mode == 1, CPM_ERR_ARG, "bad residual_mode");
+
+  DBuf<int32_t> err(1);
+  CPM_CUDA_TRY(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), st));
+  for (int l = 0; l + 1 < nl; ++l) {
+    build_transfer(*H->L[l + 1].lev, *H->L[l].lev, H->L[l].R, st, err.get());
+    build_transfer(*H->L[l].lev, *H->L[l + 1].lev, H->L[l].P, st, err.get());
+  }
+  // per-point c on every level (restricted from the finest band)
+  if (o.c_device) {
+    H->L[0].c64.alloc(f0.nB);
+    CPM_CUDA_TRY(cudaMemcpyAsync(H->L[0].c64.get(), o.c_device, sizeof(double) * f0.nB,
+                                 cudaMemcpyDeviceToDevice, st));
+    for (int l = 0; l + 1 < nl; ++l) {
+      HLevel& a = H->L[l];
+      HLevel& b = H->L[l + 1];
+      b.c64.alloc(b.lev->nB);
+      launch_transfer<double>(tview<double>(a.R, *a.lev, a.lev->dim), a.c64.get(), b.c64.get(), false, st);
+    }
+    for (auto& lv : H->L) {
+      lv.c32.alloc(lv.lev->nB);
+      launch_cast_from_f64<float>(lv.c64.get(), lv.c32.get(), lv.lev->nB, st);
+    }
+  }
+  // diag(A) = c - diag(M), work buffers
+  for (auto& lv : H->L) {
+    const int64_t nB = lv.lev->nB, np = lv.lev->nplus();
+    DBuf<double> dM(nB);
+    launch_diag_M(lv.view<double>(), dM.get(), st);
+    lv.dA64.alloc(nB);
+    lv.dA32.alloc(nB);
+    k_diag_A<<<nblk(nB, 256), 256, 0, st>>>(dM.get(), lv.c64.get(), H->c, lv.dA64.get(),
+                                            lv.dA32.get(), nB);
+    CPM_CUDA_TRY(cudaGetLastError());
+    CPM_CUDA_TRY(cudaStreamSynchronize(st));
+    lv.w64.alloc(nB, np);
+    lv.w32.alloc(nB, np);
+  }
+  // coarsest: dense A = diag(c) - M, inverted in place (FP64)
+  H->nc = cl.nB;
+  if (H->coarse_sweeps == 0) {
+    H->Ainv.alloc((size_t)H->nc * H->nc);
+    CPM_CUDA_TRY(cudaMemsetAsync(H->Ainv.get(), 0, sizeof(double) * (size_t)H->nc * H->nc, st));
+    launch_assemble_A(H->L[nl - 1].view<double>(), H->L[nl - 1].c64.get(), H->c, H->Ainv.get(), st);
+    CPM_CUDA_TRY(cudaGetLastError());
+    invert_dense(H->Ainv.get(), H->nc, st, err.get());
+  }
+  int32_t herr = 0;
+  CPM_CUDA_TRY(cudaMemcpyAsync(&herr, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  CPM_CHECK(!(herr & 4), CPM_ERR_REACH, "a transfer stencil leaves the source band");
+  CPM_CHECK(!(herr & 1), CPM_ERR_SINGULAR, "coarsest-level matrix is singular");
+
+  // solve buffers
+  const int64_t nB0 = f0.nB;
+  H->part_blocks = (int)std::max<int64_t>(nblk(nB0, 256), kNormBlocks);
+  H->part.alloc(2 * (size_t)H->part_blocks);
+  H->norms.alloc(4);
+  H->normf.alloc(4);
+  H->u_own.alloc(nB0);
+  H->f_own.alloc(nB0);
+  H->r64.alloc(nB0);
+  H->d64.alloc(nB0);
+  H->r32.alloc(nB0);
+  H->d32.alloc(nB0);
+  CPM_CUDA_TRY(cudaStreamCreateWithFlags(&H->hs, cudaStreamNonBlocking));
+  CPM_CUDA_TRY(cudaEventCreateWithFlags(&H->ev, cudaEventDisableTiming));
+  CPM_CUDA_TRY(cudaMallocHost(&H->pinned, 8 * sizeof(double)));
+  *out = H.release();
+  CPM_API_END
+}
+
+cpm_status cpm_hier_info(cpm_hier h, int32_t* n_levels, int32_t level, int64_t* n_band) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr, CPM_ERR_ARG, "hierarchy is NULL");
+  if (n_levels) *n_levels = (int32_t)h->L.size();
+  if (n_band) {
+    CPM_CHECK(level >= 0 && level < (int)h->L.size(), CPM_ERR_ARG, "level out of range");
+    *n_band = h->L[level].lev->nB;
+  }
+  CPM_API_END
+}
+
+cpm_status cpm_apply(cpm_hier h, int32_t level, int32_t prec, const void* u, void* Mu,
+                     cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr && u != nullptr && Mu != nullptr, CPM_ERR_ARG, "NULL argument");
+  CPM_CHECK(level >= 0 && level < (int)h->L.size(), CPM_ERR_ARG, "level out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  HLevel& lv = h->L[level];
+  if (prec == CPM_F64) {
+    const auto v = lv.view<double>();
+    launch_extend<double>(v, (const double*)u, lv.w64.w.get(), (int32_t)v.nplus, st);
+    launch_lap<double>(v, LAP_APPLY, (const double*)u, lv.w64.w.get(), nullptr, nullptr, 0.0, nullptr,
+                       0.0, (double*)Mu, nullptr, nullptr, 0, st);
+  } else {
+    CPM_CHECK(prec == CPM_F32, CPM_ERR_ARG, "unknown precision");
+    const auto v = lv.view<float>();
+    launch_extend<float>(v, (const float*)u, lv.w32.w.get(), (int32_t)v.nplus, st);
+    launch_lap<float>(v, LAP_APPLY, (const float*)u, lv.w32.w.get(), nullptr, nullptr, 0.f, nullptr,
+                      0.f, (float*)Mu, nullptr, nullptr, 0, st);
+  }
+  CPM_CUDA_TRY(cudaGetLastError());
+  CPM_API_END
+}
+
+cpm_status cpm_extend(cpm_hier h, int32_t level, int32_t prec, const void* u, void* w,
+                      int32_t with_ghost, cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr && u != nullptr && w != nullptr, CPM_ERR_ARG, "NULL argument");
+  CPM_CHECK(level >= 0 && level < (int)h->L.size(), CPM_ERR_ARG, "level out of range");
+  cudaStream_t st = (cudaStream_t)stream;
+  HLevel& lv = h->L[level];
+  const int32_t np = with_ghost ? (int32_t)lv.lev->nplus() : lv.lev->nB;
+  if (prec == CPM_F64) {
+    launch_extend<double>(lv.view<double>(), (const double*)u, (double*)w, np, st);
+  } else {
+    CPM_CHECK(prec == CPM_F32, CPM_ERR_ARG, "unknown precision");
+    launch_extend<float>(lv.view<float>(), (const float*)u, (float*)w, np, st);
+  }
+  CPM_CUDA_TRY(cudaGetLastError());
+  CPM_API_END
+}
+
+int64_t cpm_kernel_launches(void) { return cpm::launches_total(); }
+
+cpm_status cpm_smooth(cpm_hier h, int32_t level, int32_t prec, const void* f, void* u,
+                      int32_t sweeps, cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr && u != nullptr && f != nullptr, CPM_ERR_ARG, "NULL argument");
+  CPM_CHECK(level >= 0 && level < (int)h->L.size(), CPM_ERR_ARG, "level out of range");
+  CPM_CHECK(sweeps >= 0, CPM_ERR_ARG, "sweeps must be >= 0");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == CPM_F64)
+    smooth<double>(h, level, (const double*)f, (double*)u, sweeps, st);
+  else {
+    CPM_CHECK(prec == CPM_F32, CPM_ERR_ARG, "unknown precision");
+    smooth<float>(h, level, (const float*)f, (float*)u, sweeps, st);
+  }
+  CPM_CUDA_TRY(cudaGetLastError());
+  CPM_API_END
+}
+
+cpm_status cpm_vcycle(cpm_hier h, int32_t prec, const void* f, void* u, cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr && u != nullptr && f != nullptr, CPM_ERR_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  if (prec == CPM_F64)
+    vcycle_level<double>(h, 0, (const double*)f, (double*)u, st);
+  else {
+    CPM_CHECK(prec == CPM_F32, CPM_ERR_ARG, "unknown precision");
+    vcycle_level<float>(h, 0, (const float*)f, (float*)u, st);
+  }
+  CPM_CUDA_TRY(cudaGetLastError());
+  CPM_API_END
+}
+
+cpm_status cpm_residual_norms(cpm_hier h, const double* f, const double* u, double* rel_inf,
+                              double* abs_l2, cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr && u != nullptr && f != nullptr, CPM_ERR_ARG, "NULL argument");
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t nB = h->L[0].lev->nB;
+  launch_norm_partials<double>(f, nB, h->part.get(), st);
+  launch_norm_final(h->part.get(), kNormBlocks, h->normf.get(), st);
+  outer_residual(h, f, u, h->r64.get(), st);
+  double hn[3], hf[3];
+  CPM_CUDA_TRY(cudaMemcpyAsync(hn, h->norms.get(), 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaMemcpyAsync(hf, h->normf.get(), 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (rel_inf) *rel_inf = hf[0] > 0 ? hn[0] / hf[0] : hn[0];
+  if (abs_l2) *abs_l2 = std::sqrt(hn[1]);
+  CPM_API_END
+}
+
+cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opts* opts_in,
+                     cpm_solve_report* report, cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr && u != nullptr && f != nullptr, CPM_ERR_ARG, "NULL argument");
+  cpm_solve_opts o{};
+  o.use_graph = 1;
+  if (opts_in) o = *opts_in;
+  if (!(o.tol > 0)) o.tol = 1e-10;
+  if (o.inner_cycles <= 0) o.inner_cycles = 1;
+  CPM_CHECK(o.inner_cycles <= 16, CPM_ERR_ARG, "inner_cycles must be <= 16");
+  if (o.max_iter <= 0) o.max_iter = 100;
+  CPM_CHECK(o.mode == CPM_SOLVE_F64 || o.mode == CPM_SOLVE_MIXED, CPM_ERR_ARG, "unknown mode");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t us = (cudaStream_t)stream;
+  cudaStream_t st = h->hs;
+  const int64_t nB = h->L[0].lev->nB;
+  CPM_CUDA_TRY(cudaEventRecord(h->ev, us));
+  CPM_CUDA_TRY(cudaStreamWaitEvent(st, h->ev, 0));
+  CPM_CUDA_TRY(cudaMemcpyAsync(h->f_own.get(), f, nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  if (o.zero_init)
+    CPM_CUDA_TRY(cudaMemsetAsync(h->u_own.get(), 0, nB * sizeof(double), st));
+  else
+    CPM_CUDA_TRY(cudaMemcpyAsync(h->u_own.get(), u, nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_norm_partials<double>(h->f_own.get(), nB, h->part.get(), st);
+  launch_norm_final(h->part.get(), kNormBlocks, h->normf.get(), st);
+  CPM_CUDA_TRY(cudaMemcpyAsync(h->pinned + 4, h->normf.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
+  outer_residual(h, h->f_own.get(), h->u_own.get(), h->r64.get(), st);
+  CPM_CUDA_TRY(cudaMemcpyAsync(h->pinned, h->norms.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  const double fmax = h->pinned[4];
+  CPM_CHECK(std::isfinite(fmax), CPM_ERR_ARG, "f is not finite");
+  const double fn = fmax > 0 ? fmax : 1.0;
+  cudaGraphExec_t& gx = h->graph[o.mode];
+  if (gx && h->graph_inner[o.mode] != o.inner_cycles) {
+    cudaGraphExecDestroy(gx);
+    gx = nullptr;
+  }
+  if (o.use_graph && !gx) {
+    h->graph_inner[o.mode] = o.inner_cycles;
+    cudaGraph_t g;
+    CPM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    set_capturing(true);
+    try {
+      outer_step(h, o.mode, o.inner_cycles, st);
+    } catch (...) {
+      set_capturing(false);
+      cudaStreamEndCapture(st, &g);
+      throw;
+    }
+    set_capturing(false);
+    CPM_CUDA_TRY(cudaStreamEndCapture(st, &g));
+    size_t nn = 0;
+    CPM_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &nn));
+    std::vector<cudaGraphNode_t> nodes(nn);
+    CPM_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &nn));
+    int64_t nk = 0;
+    for (auto nd : nodes) {
+      cudaGraphNodeType t;
+      CPM_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+      nk += t == cudaGraphNodeTypeKernel;
+    }
+    h->graph_kernels[o.mode] = nk;
+    CPM_CUDA_TRY(cudaGraphInstantiate(&gx, g, 0));
+    CPM_CUDA_TRY(cudaGraphDestroy(g));
+  }
+  cpm_solve_report rep{};
+  double rel = h->pinned[0] / fn, best = rel;
+  cpm_status result = CPM_ERR_NOT_CONVERGED;
+  int it = 0;
+  for (;; ++it) {
+    if (it < CPM_MAX_HISTORY) rep.history[it] = rel;
+    if (rel <= o.tol) { result = CPM_OK; break; }
+    if (!std::isfinite(rel) || rel > 1e3 * best) { result = CPM_ERR_DIVERGED; break; }
+    if (it >= o.max_iter) break;
+    best = std::min(best, rel);
+    if (o.use_graph) {
+      CPM_CUDA_TRY(cudaGraphLaunch(gx, st));
+      count_launch(h->graph_kernels[o.mode]);
+    } else
+      outer_step(h, o.mode, o.inner_cycles, st);
+    CPM_CUDA_TRY(cudaMemcpyAsync(h->pinned, h->norms.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
+    CPM_CUDA_TRY(cudaStreamSynchronize(st));
+    rel = h->pinned[0] / fn;
+  }
+  CPM_CUDA_TRY(cudaMemcpyAsync(u, h->u_own.get(), nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CPM_CUDA_TRY(cudaEventRecord(h->ev, st));
+  CPM_CUDA_TRY(cudaStreamWaitEvent(us, h->ev, 0));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  rep.iters = it;
+  rep.converged = result == CPM_OK;
+  rep.rel_residual = rel;
+  rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  if (report) *report = rep;
+  if (result != CPM_OK) {
+    cpm::set_last_error(result == CPM_ERR_DIVERGED ? "residual diverged" : "max_iter reached");
+    return result;
+  }
+  CPM_API_END
+}
+
+cpm_status cpm_hier_destroy(cpm_hier h) {
+  CPM_API_BEGIN
+  delete h;
+  CPM_API_END
+}
+
+}  // extern "C"

@@ -1,0 +1,91 @@
+// Device operators of one level (extension E, the operator M, Jacobi,
+// residuals, closest-point transfers, norms) and their launchers.
+#pragma once
+
+#include "cpm_internal.cuh"
+
+namespace cpm {
+
+// Plain-pointer view of one level for precision T.
+template <typename T>
+struct LevelView {
+  BrickView bv;
+  const uint64_t* key;  // B+ keys
+  const T* fr;          // d x nplus fractions (SoA)
+  int64_t nplus;
+  int32_t nB;
+  int dim;
+  T inv_h2;   // 1/dx^2
+  T gamma;    // 2d/dx^2
+};
+
+// Transfer records: for each target point, the base node of its linear
+// (2^d) stencil in the source grid and the fractions (SoA, d x n).
+template <typename T>
+struct TransferView {
+  const uint64_t* base;  // x | y << 16 | z << 32
+  const T* fr;
+  int32_t n;             // number of target points
+  BrickView src;         // source level bricks
+  int dim;
+};
+
+enum LapMode { LAP_APPLY = 0, LAP_RESID = 1, LAP_JACOBI = 2 };
+
+// w = E u on the first npts points of B+ (npts = nB or nB + nG).
+template <typename T>
+void launch_extend(const LevelView<T>& L, const T* u, T* w, int32_t npts, cudaStream_t st);
+
+// Stencil pass on B from w = E u:
+//   APPLY : out = M u
+//   RESID : out = f - c u + M u  (and block partials of max|out|, sum out^2
+//           into part[2*block], part[2*block+1] if part != nullptr)
+//   JACOBI: u += omega (f - c u + M u) / dA   (in place, out unused)
+template <typename T>
+void launch_lap(const LevelView<T>& L, LapMode mode, const T* u, const T* w, const T* f,
+                const T* cvec, T cval, const T* dA, T omega, T* out, T* u_inout, double* part,
+                int nblocks_part, cudaStream_t st);
+
+// RM smoother pieces: u += omega (f - (cI - L_B) u) / (c + gamma) with the
+// band-restricted Laplacian, written to out (out may not alias u).
+template <typename T>
+void launch_rm_jacobi(const LevelView<T>& L, const T* u, const T* f, const T* cvec, T cval, T omega,
+                      T* out, cudaStream_t st);
+// r = f - (cI - L_B) u
+template <typename T>
+void launch_rm_resid(const LevelView<T>& L, const T* u, const T* f, const T* cvec, T cval, T* out,
+                     cudaStream_t st);
+
+// dst[j] = sum of linear-interpolation weights times src (restriction), or
+// dst[j] += (prolongation with add).
+template <typename T>
+void launch_transfer(const TransferView<T>& tv, const T* src, T* dst, bool add, cudaStream_t st);
+
+// Norm partials of a vector and the final reduction to out[0] = max|x|,
+// out[1] = sum x^2 (device doubles).
+constexpr int kNormBlocks = 1216;  // 152 SMs x 8
+template <typename T>
+void launch_norm_partials(const T* x, int64_t n, double* part, cudaStream_t st);
+void launch_norm_final(const double* part, int nblocks, double* out, cudaStream_t st);
+
+// Mixed precision helpers.
+void launch_scale_to_f32(const double* r, const double* norms, float* r32, int64_t n, cudaStream_t st);
+void launch_axpy_scaled(double* u, const float* d, const double* norms, int64_t n, cudaStream_t st);
+void launch_axpy64(double* u, const double* d, int64_t n, cudaStream_t st);
+template <typename T>
+void launch_cast_to_f64(const T* x, double* y, int64_t n, cudaStream_t st);
+template <typename T>
+void launch_cast_from_f64(const double* x, T* y, int64_t n, cudaStream_t st);
+
+// Coarsest direct solve x = Ainv b (FP64 matrix, FP64 accumulation).
+template <typename T>
+void launch_coarse_gemv(const double* Ainv, const T* b, T* x, int32_t n, cudaStream_t st);
+
+// Setup kernels.
+void launch_diag_M(const LevelView<double>& L, double* diagM, cudaStream_t st);
+void launch_assemble_A(const LevelView<double>& L, const double* cvec, double cval, double* A,
+                       cudaStream_t st);
+// In-place Gauss-Jordan inversion with partial pivoting (row-major n x n).
+void invert_dense(double* A, int32_t n, cudaStream_t st, int32_t* err);
+
+}  // namespace cpm

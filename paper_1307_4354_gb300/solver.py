@@ -1,0 +1,166 @@
+"""Torch-facing wrappers over the C ABI (device memory and streams only).
+
+``Band`` and ``Hierarchy`` own the C handles; vectors are CUDA tensors in the
+library's band order (float64 or float32).  Nothing here computes: every
+step of the method runs in libcpm.so.
+"""
+from __future__ import annotations
+
+import numpy as np
+import torch
+
+from . import capi
+
+_KINDS = {"circle": capi.CPM_CIRCLE, "sphere": capi.CPM_SPHERE, "torus": capi.CPM_TORUS,
+          "ellipsoid": capi.CPM_ELLIPSOID}
+_SMOOTHERS = {"jacobi": capi.CPM_SMOOTH_JACOBI, "rm": capi.CPM_SMOOTH_RM}
+
+
+def make_surface(kind: str, *params: float) -> capi.cpm_surface:
+    s = capi.cpm_surface()
+    s.kind = _KINDS[kind]
+    for i, p in enumerate(params):
+        s.param[i] = float(p)
+    if kind in ("circle", "sphere") and not params:
+        s.param[0] = 1.0
+    return s
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, torch.cuda.Stream):
+        return stream.cuda_stream
+    return int(stream)
+
+
+def _ptr(t: torch.Tensor, dtype, n: int) -> int:
+    if not t.is_cuda or t.dtype != dtype or not t.is_contiguous() or t.numel() != n:
+        raise ValueError(f"expected a contiguous CUDA {dtype} tensor of {n} elements")
+    return t.data_ptr()
+
+
+class Band:
+    """Band B and ghost ring of one surface at spacing dx (cpm_build_band)."""
+
+    def __init__(self, kind: str, params=(), dx: float = 1 / 64, lo: float = -2.0,
+                 lambda2: float = 0.0, stream=None):
+        self.kind = kind
+        self.params = tuple(params)
+        self.dim = 2 if kind == "circle" else 3
+        self.dx = dx
+        self.lo = lo
+        g = capi.cpm_grid()
+        g.lo, g.dx, g.n, g.lambda2 = lo, dx, 0, lambda2
+        self.handle = capi.cpm_build_band(make_surface(kind, *self.params), g, _stream(stream))
+        self.nb, self.ng = capi.cpm_band_info(self.handle)
+
+    def export(self):
+        """(ijk, cp, stencil_base) of B+ (B first, then G) as numpy arrays."""
+        n = self.nb + self.ng
+        ijk = np.empty((n, self.dim), np.int32)
+        cp = np.empty((n, self.dim), np.float64)
+        base = np.empty((n, self.dim), np.int32)
+        capi.cpm_band_export(self.handle, ijk.ctypes.data, cp.ctypes.data, base.ctypes.data)
+        return ijk, cp, base
+
+    def close(self):
+        if getattr(self, "handle", None):
+            capi.cpm_band_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Hierarchy:
+    """Multigrid hierarchy on a band (cpm_build_hierarchy) and its operators."""
+
+    def __init__(self, band: Band, coarsest_dx: float = 0.0, nu1: int = 3, nu2: int = 3,
+                 omega: float = 0.8, smoother: str = "jacobi", c: float = 1.0,
+                 c_device: torch.Tensor | None = None, residual: str = "extended",
+                 coarse_sweeps: int = 0, stream=None):
+        o = capi.cpm_mg_opts()
+        o.coarsest_dx, o.nu1, o.nu2, o.omega = coarsest_dx, nu1, nu2, omega
+        o.smoother, o.transfer_deg, o.c = _SMOOTHERS[smoother], 1, c
+        o.residual_mode = {"extended": capi.CPM_RESID_EXTENDED, "plain": capi.CPM_RESID_PLAIN}[residual]
+        o.coarse_sweeps = coarse_sweeps
+        o.c_device = _ptr(c_device, torch.float64, band.nb) if c_device is not None else None
+        self.band = band
+        self.handle = capi.cpm_build_hierarchy(band.handle, o, _stream(stream))
+        self.n_levels, self.nb = capi.cpm_hier_info(self.handle, 0)
+
+    def level_size(self, level: int) -> int:
+        return capi.cpm_hier_info(self.handle, level)[1]
+
+    def apply(self, u: torch.Tensor, level: int = 0, out: torch.Tensor | None = None, stream=None):
+        n = self.level_size(level)
+        prec = capi.CPM_F64 if u.dtype == torch.float64 else capi.CPM_F32
+        out = torch.empty_like(u) if out is None else out
+        capi.cpm_apply(self.handle, level, prec, _ptr(u, u.dtype, n), _ptr(out, u.dtype, n), _stream(stream))
+        return out
+
+    def extend(self, u: torch.Tensor, level: int = 0, with_ghost: bool = False,
+               out: torch.Tensor | None = None, stream=None):
+        """w = E u on B (and the ghost ring when with_ghost)."""
+        n = self.level_size(level)
+        nw = n + (self.ghost_size(level) if with_ghost else 0)
+        prec = capi.CPM_F64 if u.dtype == torch.float64 else capi.CPM_F32
+        out = torch.empty(nw, dtype=u.dtype, device=u.device) if out is None else out
+        capi.cpm_extend(self.handle, level, prec, _ptr(u, u.dtype, n), _ptr(out, u.dtype, nw),
+                        with_ghost, _stream(stream))
+        return out
+
+    def ghost_size(self, level: int) -> int:
+        if level == 0:
+            return self.band.ng
+        raise ValueError("ghost sizes of coarse levels are not exported")
+
+    def smooth(self, f: torch.Tensor, u: torch.Tensor, sweeps: int = 1, level: int = 0, stream=None):
+        n = self.level_size(level)
+        prec = capi.CPM_F64 if u.dtype == torch.float64 else capi.CPM_F32
+        capi.cpm_smooth(self.handle, level, prec, _ptr(f, u.dtype, n), _ptr(u, u.dtype, n), sweeps,
+                        _stream(stream))
+        return u
+
+    def vcycle(self, f: torch.Tensor, u: torch.Tensor, stream=None):
+        prec = capi.CPM_F64 if u.dtype == torch.float64 else capi.CPM_F32
+        capi.cpm_vcycle(self.handle, prec, _ptr(f, u.dtype, self.nb), _ptr(u, u.dtype, self.nb),
+                        _stream(stream))
+        return u
+
+    def solve(self, f: torch.Tensor, u: torch.Tensor | None = None, tol: float = 1e-10,
+              max_iter: int = 100, mode: str = "f64", use_graph: bool = True, stream=None,
+              raise_on_fail: bool = True, inner_cycles: int = 1, zero_init: bool | None = None):
+        zero = u is None if zero_init is None else bool(zero_init)
+        if u is None:
+            u = torch.empty_like(f)
+        o = capi.cpm_solve_opts()
+        o.tol, o.max_iter = tol, max_iter
+        o.mode = capi.CPM_SOLVE_MIXED if mode == "mixed" else capi.CPM_SOLVE_F64
+        o.use_graph, o.zero_init = int(use_graph), int(zero)
+        o.inner_cycles = inner_cycles
+        st, rep = capi.cpm_solve(self.handle, _ptr(f, torch.float64, self.nb),
+                                 _ptr(u, torch.float64, self.nb), o, _stream(stream), raise_on_fail)
+        n = min(rep.iters + 1, capi.CPM_MAX_HISTORY)
+        return u, {"status": st, "iters": rep.iters, "converged": bool(rep.converged),
+                   "rel_residual": rep.rel_residual, "history": list(rep.history[:n]),
+                   "seconds": rep.seconds}
+
+    def residual_norms(self, f: torch.Tensor, u: torch.Tensor, stream=None):
+        return capi.cpm_residual_norms(self.handle, _ptr(f, torch.float64, self.nb),
+                                       _ptr(u, torch.float64, self.nb), _stream(stream))
+
+    def close(self):
+        if getattr(self, "handle", None):
+            capi.cpm_hier_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

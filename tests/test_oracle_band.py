@@ -95,3 +95,17 @@ def test_ellipsoid_reduces_to_sphere():
 def test_circle_band_size():
     """Circle at dx = 1/64: 2912 band points (the circle workload)."""
     assert build_band(circle(), 1.0 / 64).nb == 2912
+
+
+def test_ellipsoid_medial_disk_is_far():
+    """Nodes on the ellipsoid's medial disk (smallest axis coordinate 0, inside)
+    have no stationary point of the secular equation above -min a^2; they are
+    at least the reach away from S (brute force over a dense surface sample)."""
+    surf = ellipsoid(1.1, 0.8, 0.7)
+    X = np.array([[0.25, 0.0, 0.0], [0.3, 0.05, 0.0]])
+    _, d2 = closest_point(surf, X)
+    assert np.all(np.isinf(d2))
+    th, ph = np.meshgrid(np.linspace(0, 2 * np.pi, 721), np.linspace(0, np.pi, 361))
+    Y = np.stack([1.1 * np.sin(ph) * np.cos(th), 0.8 * np.sin(ph) * np.sin(th), 0.7 * np.cos(ph)], -1).reshape(-1, 3)
+    for x in X:
+        assert np.sqrt(((Y - x) ** 2).sum(1)).min() >= surf.reach * 0.99
