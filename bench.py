@@ -324,6 +324,47 @@ def run_cpm(args, world, rank, local):
     print(json.dumps(line), flush=True)
 
 
+def run_micro(args):
+    """Kernel micro-benchmark on the dx = 1/256 sphere band (also the ncu target):
+    the extension over B+ in FP32 and FP64 and the operator M (extension +
+    stencil), each timed with CUDA events on the launching stream."""
+    import torch
+
+    import paper_1307_4354_gb300 as pkg
+
+    pkg.build()
+    band = pkg.Band("sphere", (), DX)
+    H = pkg.Hierarchy(band, coarsest_dx=2 * DX, coarse_sweeps=1)
+    nb, ng = band.nb, band.ng
+    g = torch.Generator(device="cuda").manual_seed(0)
+    u64 = torch.rand(nb, dtype=torch.float64, device="cuda", generator=g) * 2 - 1
+    u32 = u64.float()
+    w64 = torch.empty(nb + ng, dtype=torch.float64, device="cuda")
+    w32 = torch.empty(nb + ng, dtype=torch.float32, device="cuda")
+    m64 = torch.empty_like(u64)
+    m32 = torch.empty_like(u32)
+    st = torch.cuda.current_stream()
+    cases = {"extend32": lambda: H.extend(u32, with_ghost=True, out=w32),
+             "extend64": lambda: H.extend(u64, with_ghost=True, out=w64),
+             "apply32": lambda: H.apply(u32, out=m32),
+             "apply64": lambda: H.apply(u64, out=m64)}
+    out = {}
+    for name, fn in cases.items():
+        if args.micro != "all" and args.micro != name:
+            continue
+        for _ in range(args.warmup):
+            fn()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record(st)
+        for _ in range(args.steps):
+            fn()
+        e1.record(st)
+        torch.cuda.synchronize()
+        out[name + "_ms"] = e0.elapsed_time(e1) / args.steps
+    print(json.dumps({"micro": out, "nb": nb, "ng": ng}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -332,8 +373,13 @@ def main():
     ap.add_argument("--impl", default="cpm", choices=["cpm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inner", type=int, default=1, help="FP32 V-cycles per outer iteration")
+    ap.add_argument("--micro", default=None,
+                    help="kernel micro-benchmark instead of the solve: extend32|extend64|apply32|apply64|all")
     args = ap.parse_args()
     world, rank, local = dist_setup()
+    if args.micro:
+        run_micro(args)
+        return
     if args.impl == "reference":
         run_reference(args, world, rank)
     else:

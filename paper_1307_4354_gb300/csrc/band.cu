@@ -459,6 +459,21 @@ __global__ void k_check_stencils(BrickView v, const uint64_t* key, int64_t nplus
         }
 }
 
+// 8. Laplacian neighbours of B (order -x, +x, -y, +y, -z, +z), as B+ indices.
+__global__ void k_neighbours(BrickView v, const uint64_t* key, int32_t nB, int dim, int32_t* nbr,
+                             int32_t* err) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nB) return;
+  const uint64_t k = key[i];
+  const int x = key_x(k), y = key_y(k), z = key_z(k);
+  const int d[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  for (int q = 0; q < 2 * dim; ++q) {
+    const int32_t j = node_index(v, x + d[q][0], y + d[q][1], z + d[q][2]);
+    if (j < 0) atomicOr(err, 16);
+    nbr[(int64_t)q * nB + i] = j < 0 ? i : j;
+  }
+}
+
 // ----------------------------------------------------------------- driver
 static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -570,6 +585,16 @@ void build_level(const cpm_surface& surf, double lo, double dx, int n, double la
   int32_t herr = 0;
   CPM_CUDA_TRY(cudaMemcpyAsync(&herr, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (herr == 0) {
+    build_ext_tiles(L, st);
+    L.nbr.alloc((size_t)2 * dim * L.nB);
+    k_neighbours<<<blocks_for(L.nB, 256), 256, 0, st>>>(L.view(), L.key.get(), L.nB, dim, L.nbr.get(),
+                                                        err.get());
+    CPM_CUDA_TRY(cudaGetLastError());
+    CPM_CUDA_TRY(cudaMemcpyAsync(&herr, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CPM_CUDA_TRY(cudaStreamSynchronize(st));
+    CPM_CHECK(herr == 0, CPM_ERR_CHECKED, "a Laplacian neighbour of the band is missing from B+");
+  }
   CPM_CHECK(!(herr & 8), CPM_ERR_ARG, "the band touches the edge of the grid (enlarge the domain)");
   if (herr & 1) {
     double ei[8];

@@ -152,6 +152,15 @@ struct Level {
   DBuf<double> cp;    // d x (nB+nG), SoA
   DBuf<double> fr64;  // d x (nB+nG), SoA
   DBuf<float> fr32;   // d x (nB+nG), SoA
+  // extension tiles: the points of B (then of G) grouped by the brick that
+  // holds their cubic stencil base ("E order"); see ext.cu
+  int32_t ntiles_B = 0, ntiles = 0;
+  DBuf<uint32_t> tile_brick;  // packed brick coordinates of each tile
+  DBuf<int32_t> tile_start;   // ntiles + 1 offsets into the E-order arrays
+  DBuf<uint32_t> erec;        // band index << 6 | stencil base inside the brick
+  DBuf<float> efr32;          // d x (nB+nG) fractions in E order
+  DBuf<double> ew64;          // 4d x (nB+nG) FP64 cubic weights in E order
+  DBuf<int32_t> nbr;          // 2d x nB: B+ index of the Laplacian neighbours of B
 
   BrickView view() const {
     BrickView v;
@@ -166,6 +175,8 @@ struct Level {
 // Build the band of one level (band.cu).  Throws cpm::Error.
 void build_level(const cpm_surface& s, double lo, double dx, int n, double lambda2,
                  cudaStream_t st, Level& out);
+// Group the points of a level into extension tiles (ext.cu).
+void build_ext_tiles(Level& L, cudaStream_t st);
 
 // Host counter of solve-path kernel launches (cpm_kernel_launches).  While a
 // stream capture is being recorded the launch helpers do not count; a graph

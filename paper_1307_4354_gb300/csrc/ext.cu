@@ -1,0 +1,256 @@
+// Closest-point extension w = E u (Sec. 3.1, Eq. 3.1; the re-extension of
+// Eq. 4.2b): w_i = sum over the 4^d stencil nodes of cp(x_i) of the tensor
+// product of 1-D cubic Lagrange weights times u.
+//
+// Tiling.  The points of B (then, separately, of the ghost ring G) are grouped
+// by the 4^d brick that holds their stencil base node.  A tile's stencils all
+// lie in the fixed 7^d box starting at the brick's first node, so one CTA
+// stages that box from HBM/L2 into shared memory once (with the brick map and
+// occupancy masks) and evaluates every point of the tile from it.  Each box
+// row is stored as the four 16-byte-aligned windows of 4 consecutive values a
+// stencil run can start at, so one run of the stencil is one vector load from
+// shared memory.  Records are stored in this "E order" (band index and base
+// position inside the brick in one 32-bit word, fractions SoA); results are
+// written back to the band index.
+#include "ops.cuh"
+
+namespace cpm {
+
+static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ----------------------------------------------------------------- tile build
+__global__ void k_tile_slots(BrickView v, const uint64_t* key, int64_t nplus, int32_t nB,
+                             int32_t nbricks, int dim, int32_t* slot, int64_t* count, int32_t* err) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nplus) return;
+  const uint64_t k = key[i];
+  const int bx = key_x(k) + key_ox(k), by = key_y(k) + key_oy(k);
+  const int bz = dim == 3 ? key_z(k) + key_oz(k) : 0;
+  int32_t b = -1;
+  if (bx >= 0 && by >= 0 && bz >= 0 && bx < v.n && by < v.n && bz < v.n)
+    b = v.map[((size_t)(bz >> 2) * v.nby + (by >> 2)) * v.nbx + (bx >> 2)];
+  if (b < 0) {
+    atomicOr(err, 1);
+    slot[i] = -1;
+    return;
+  }
+  const int32_t s = (i < nB ? 0 : nbricks) + b;
+  slot[i] = s;
+  atomicAdd(reinterpret_cast<unsigned long long*>(count + s), 1ull);
+}
+
+__global__ void k_tile_flags(const int64_t* count, int64_t n, int64_t* flag) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) flag[i] = count[i] > 0;
+}
+
+__global__ void k_tile_emit(const int64_t* count, const int64_t* offset, const int64_t* tpos,
+                            const uint32_t* bcoord, int64_t n, int32_t nbricks, uint32_t* tile_brick,
+                            int32_t* tile_start) {
+  const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (s >= n || count[s] == 0) return;
+  const int64_t t = tpos[s];
+  tile_brick[t] = bcoord[s % nbricks];
+  tile_start[t] = (int32_t)offset[s];
+}
+
+__global__ void k_tile_scatter(const uint64_t* key, const int32_t* slot, const int64_t* offset,
+                               int64_t* cursor, int64_t nplus, int dim, const double* fr64,
+                               uint32_t* erec, float* efr32, double* ew64) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nplus) return;
+  const int32_t s = slot[i];
+  if (s < 0) return;
+  const int64_t pos =
+      offset[s] + (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(cursor + s), 1ull);
+  const uint64_t k = key[i];
+  const int bx = key_x(k) + key_ox(k), by = key_y(k) + key_oy(k);
+  const int bz = dim == 3 ? key_z(k) + key_oz(k) : 0;
+  erec[pos] = ((uint32_t)i << 6) | (uint32_t)((bx & 3) | ((by & 3) << 2) | ((bz & 3) << 4));
+  for (int a = 0; a < dim; ++a) {
+    const double sf = fr64[a * nplus + i];
+    efr32[a * nplus + pos] = (float)sf;
+    // 1-D cubic Lagrange weights at nodes -1, 0, 1, 2 (proof of Theorem 3.3)
+    const double sm1 = sf - 1.0, sm2 = sf - 2.0, sp1 = sf + 1.0;
+    const double p = sf * sm1, q = sp1 * sm2;
+    ew64[(4 * a + 0) * nplus + pos] = -(p * sm2) * (1.0 / 6.0);
+    ew64[(4 * a + 1) * nplus + pos] = (q * sm1) * 0.5;
+    ew64[(4 * a + 2) * nplus + pos] = -(q * sf) * 0.5;
+    ew64[(4 * a + 3) * nplus + pos] = (p * sp1) * (1.0 / 6.0);
+  }
+}
+
+void build_ext_tiles(Level& L, cudaStream_t st) {
+  const int64_t np = L.nplus();
+  CPM_CHECK(np < (1ll << 26), CPM_ERR_ARG, "more than 2^26 points on one level");
+  const int64_t nslots = 2 * (int64_t)L.nbricks;
+  DBuf<int32_t> slot(np);
+  DBuf<int64_t> count(nslots), offset(nslots), cursor(nslots), tpos(nslots);
+  DBuf<int32_t> err(1);
+  CPM_CUDA_TRY(cudaMemsetAsync(count.get(), 0, nslots * sizeof(int64_t), st));
+  CPM_CUDA_TRY(cudaMemsetAsync(cursor.get(), 0, nslots * sizeof(int64_t), st));
+  CPM_CUDA_TRY(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), st));
+  k_tile_slots<<<nblk(np, 256), 256, 0, st>>>(L.view(), L.key.get(), np, L.nB, L.nbricks, L.dim,
+                                              slot.get(), count.get(), err.get());
+  CPM_CUDA_TRY(cudaGetLastError());
+  CPM_CUDA_TRY(cudaMemcpyAsync(offset.get(), count.get(), nslots * sizeof(int64_t),
+                               cudaMemcpyDeviceToDevice, st));
+  scan_exclusive_i64(offset.get(), nslots, st);
+  k_tile_flags<<<nblk(nslots, 256), 256, 0, st>>>(count.get(), nslots, tpos.get());
+  const int64_t ntiles = scan_exclusive_i64(tpos.get(), nslots, st);
+  // tiles of B come first (slots < nbricks)
+  int64_t ntB = 0;
+  if (L.nbricks > 0) {
+    int64_t last_pos = 0, last_cnt = 0;
+    CPM_CUDA_TRY(cudaMemcpyAsync(&last_pos, tpos.get() + L.nbricks - 1, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, st));
+    CPM_CUDA_TRY(cudaMemcpyAsync(&last_cnt, count.get() + L.nbricks - 1, sizeof(int64_t),
+                                 cudaMemcpyDeviceToHost, st));
+    CPM_CUDA_TRY(cudaStreamSynchronize(st));
+    ntB = last_pos + (last_cnt > 0);
+  }
+  L.ntiles = (int32_t)ntiles;
+  L.ntiles_B = (int32_t)ntB;
+  L.tile_brick.alloc(ntiles);
+  L.tile_start.alloc(ntiles + 1);
+  k_tile_emit<<<nblk(nslots, 256), 256, 0, st>>>(count.get(), offset.get(), tpos.get(),
+                                                 L.bcoord.get(), nslots, L.nbricks, L.tile_brick.get(),
+                                                 L.tile_start.get());
+  const int32_t npi = (int32_t)np;
+  CPM_CUDA_TRY(cudaMemcpyAsync(L.tile_start.get() + ntiles, &npi, sizeof(int32_t),
+                               cudaMemcpyHostToDevice, st));
+  L.erec.alloc(np);
+  L.efr32.alloc((size_t)L.dim * np);
+  L.ew64.alloc((size_t)4 * L.dim * np);
+  k_tile_scatter<<<nblk(np, 256), 256, 0, st>>>(L.key.get(), slot.get(), offset.get(), cursor.get(),
+                                                np, L.dim, L.fr64.get(), L.erec.get(),
+                                                L.efr32.get(), L.ew64.get());
+  CPM_CUDA_TRY(cudaGetLastError());
+  int32_t herr = 0;
+  CPM_CUDA_TRY(cudaMemcpyAsync(&herr, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  CPM_CHECK(herr == 0, CPM_ERR_REACH, "a stencil base node is not a band node");
+}
+
+// ----------------------------------------------------------------- extension
+// Four consecutive values from a 16-byte-aligned shared-memory window.
+__device__ __forceinline__ void load4(const float* p, float v[4]) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v[0] = q.x; v[1] = q.y; v[2] = q.z; v[3] = q.w;
+}
+__device__ __forceinline__ void load4(const double* p, double v[4]) {
+  const double2 a = *reinterpret_cast<const double2*>(p);
+  const double2 b = *reinterpret_cast<const double2*>(p + 2);
+  v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
+}
+
+constexpr int kExtThreads = 64;
+
+template <typename T>
+__device__ __forceinline__ T dot4(const T w[4], const T* v) {
+  return w[0] * v[0] + w[1] * v[1] + w[2] * v[2] + w[3] * v[3];
+}
+
+// One CTA per tile.  Shared memory: NZ*7 rows x 4 windows x 4 values.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, const T* __restrict__ u,
+                                                              T* __restrict__ w) {
+  constexpr int NZ = DIM == 3 ? 7 : 1;
+  constexpr int NROWS = NZ * 7;
+  constexpr int NB = DIM == 3 ? 8 : 4;  // bricks overlapping the box
+  // row stride 5 windows (one pad window) spreads the rows over the banks
+  __shared__ __align__(16) T win[NROWS][5][4];
+  __shared__ uint64_t sm_mask[NB];
+  __shared__ int32_t sm_start[NB];
+  const int32_t tile = blockIdx.x;
+  const uint32_t tb = __ldg(L.tile_brick + tile);
+  const int tbx = (int)(tb & 1023), tby = (int)((tb >> 10) & 1023);
+  const int tbz = DIM == 3 ? (int)((tb >> 20) & 1023) : 0;
+  // occupancy masks and band starts of the 2^d bricks the box overlaps
+  if (threadIdx.x < NB) {
+    const int j = threadIdx.x;
+    const int bx = tbx + (j & 1), by = tby + ((j >> 1) & 1), bz = tbz + (j >> 2);
+    int32_t b = -1;
+    if (bx < L.bv.nbx && by < L.bv.nby && bz < L.bv.nbz)
+      b = __ldg(L.bv.map + ((size_t)bz * L.bv.nby + by) * L.bv.nbx + bx);
+    sm_mask[j] = b >= 0 ? __ldg(L.bv.bmask + b) : 0ull;
+    sm_start[j] = b >= 0 ? __ldg(L.bv.bstart + b) : 0;
+  }
+  __syncthreads();
+  // stage the 7^d box: node (x, y, z) of the box feeds the windows x0 = x-3..x
+  for (int q = threadIdx.x; q < NROWS * 7; q += kExtThreads) {
+    const int x = q % 7, row = q / 7;
+    const int y = row % 7, z = row / 7;
+    const int j = (x >> 2) | ((y >> 2) << 1) | ((z >> 2) << 2);
+    const uint64_t m = sm_mask[j];
+    const uint64_t bit = 1ull << ((x & 3) | ((y & 3) << 2) | ((z & 3) << 4));
+    const T v = (m & bit) ? __ldg(u + sm_start[j] + __popcll(m & (bit - 1))) : T(0);
+#pragma unroll
+    for (int x0 = 0; x0 < 4; ++x0) {
+      const int e = x - x0;
+      if (e >= 0 && e < 4) win[row][x0][e] = v;
+    }
+  }
+  __syncthreads();
+  const int32_t beg = __ldg(L.tile_start + tile), end = __ldg(L.tile_start + tile + 1);
+  const int64_t np = L.nplus;
+  for (int32_t k = beg + threadIdx.x; k < end; k += kExtThreads) {
+    const uint32_t rec = __ldg(L.erec + k);
+    const int lx = rec & 3, ly = (rec >> 2) & 3, lz = (rec >> 4) & 3;
+    T wx[4], wy[4], wz[4];
+    if constexpr (sizeof(T) == 8) {
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        wx[j] = __ldg(L.ew64 + j * np + k);
+        wy[j] = __ldg(L.ew64 + (4 + j) * np + k);
+        if (DIM == 3) wz[j] = __ldg(L.ew64 + (8 + j) * np + k);
+      }
+    } else {
+      const float sx = __ldg(L.efr + k), sy = __ldg(L.efr + np + k);
+      const float sz = DIM == 3 ? __ldg(L.efr + 2 * np + k) : 0.f;
+      const float s3[3] = {sx, sy, sz};
+      float* ws[3] = {wx, wy, wz};
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const float s = s3[a], sm1 = s - 1.f, sm2 = s - 2.f, sp1 = s + 1.f;
+        const float p = s * sm1, q = sp1 * sm2;
+        ws[a][0] = -(p * sm2) * (1.f / 6.f);
+        ws[a][1] = (q * sm1) * 0.5f;
+        ws[a][2] = -(q * s) * 0.5f;
+        ws[a][3] = (p * sp1) * (1.f / 6.f);
+      }
+    }
+    T acc = T(0);
+#pragma unroll
+    for (int c = 0; c < (DIM == 3 ? 4 : 1); ++c) {
+      T accy = T(0);
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        T vv[4];
+        load4(&win[(lz + c) * 7 + ly + b][lx][0], vv);
+        accy += wy[b] * dot4(wx, vv);
+      }
+      acc += (DIM == 3 ? wz[c] : T(1)) * accy;
+    }
+    w[rec >> 6] = acc;
+  }
+}
+
+template <typename T>
+void launch_extend(const LevelView<T>& L, const T* u, T* w, int32_t npts, cudaStream_t st) {
+  if (npts <= 0) return;
+  const int32_t nt = npts > L.nB ? L.ntiles : L.ntiles_B;
+  if (nt <= 0) return;
+  if (L.dim == 3)
+    k_extend_tiles<T, 3><<<nt, kExtThreads, 0, st>>>(L, u, w);
+  else
+    k_extend_tiles<T, 2><<<nt, kExtThreads, 0, st>>>(L, u, w);
+  count_launch();
+}
+
+template void launch_extend<double>(const LevelView<double>&, const double*, double*, int32_t,
+                                    cudaStream_t);
+template void launch_extend<float>(const LevelView<float>&, const float*, float*, int32_t,
+                                   cudaStream_t);
+
+}  // namespace cpm

@@ -23,7 +23,7 @@ static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // linear stencil in the source grid and the fractions; every stencil node
 // must be a band node of the source level.
 __global__ void k_transfer_records(const double* cp, int64_t cp_stride, int32_t n, int dim,
-                                   double lo, double dx, BrickView src, uint64_t* base,
+                                   double lo, double dx, BrickView src, int32_t* src_idx,
                                    double* fr64, float* fr32, int32_t* err) {
   const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
@@ -36,25 +36,28 @@ __global__ void k_transfer_records(const double* cp, int64_t cp_stride, int32_t 
     fr64[(int64_t)a * n + j] = s;
     fr32[(int64_t)a * n + j] = (float)s;
   }
-  base[j] = (uint64_t)(uint32_t)b[0] | ((uint64_t)(uint32_t)b[1] << 16) | ((uint64_t)(uint32_t)b[2] << 32);
   for (int c = 0; c < (dim == 3 ? 2 : 1); ++c)
     for (int bb = 0; bb < 2; ++bb)
-      for (int a = 0; a < 2; ++a)
-        if (band_index(src, b[0] + a, b[1] + bb, b[2] + c) < 0) atomicOr(err, 4);
+      for (int a = 0; a < 2; ++a) {
+        const int32_t idx = band_index(src, b[0] + a, b[1] + bb, b[2] + c);
+        if (idx < 0) atomicOr(err, 4);
+        src_idx[(int64_t)(4 * c + 2 * bb + a) * n + j] = idx < 0 ? 0 : idx;
+      }
 }
 
 // dA = c - diag(M) in FP64 and FP32.
-__global__ void k_diag_A(const double* diagM, const double* cvec, double cval, double* dA64,
-                         float* dA32, int64_t n) {
+// wdA = omega / (c - diag(M)): the Jacobi step size (Eq. 4.1), FP64 and FP32.
+__global__ void k_diag_A(const double* diagM, const double* cvec, double cval, double omega,
+                         double* dA64, float* dA32, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
-  const double v = (cvec ? cvec[i] : cval) - diagM[i];
+  const double v = omega / ((cvec ? cvec[i] : cval) - diagM[i]);
   dA64[i] = v;
   dA32[i] = (float)v;
 }
 
 struct Transfer {
-  DBuf<uint64_t> base;
+  DBuf<int32_t> src_idx;
   DBuf<double> fr64;
   DBuf<float> fr32;
   int32_t n = 0;
@@ -76,7 +79,7 @@ struct HLevel {
   std::unique_ptr<Level> lev;
   DBuf<double> c64;   // per-point c (empty: scalar)
   DBuf<float> c32;
-  DBuf<double> dA64;  // c - diag(M)
+  DBuf<double> dA64;  // omega / (c - diag(M))
   DBuf<float> dA32;
   Transfer R;  // restriction: targets = B of level l+1, source = this level
   Transfer P;  // prolongation: targets = B of this level, source = level l+1
@@ -104,6 +107,14 @@ LevelView<double> HLevel::view<double>() const {
   v.dim = lev->dim;
   v.inv_h2 = 1.0 / (lev->dx * lev->dx);
   v.gamma = 2.0 * lev->dim / (lev->dx * lev->dx);
+  v.tile_brick = lev->tile_brick.get();
+  v.tile_start = lev->tile_start.get();
+  v.erec = lev->erec.get();
+  v.efr = lev->efr32.get();
+  v.ew64 = lev->ew64.get();
+  v.ntiles_B = lev->ntiles_B;
+  v.ntiles = lev->ntiles;
+  v.nbr = lev->nbr.get();
   return v;
 }
 template <>
@@ -117,6 +128,14 @@ LevelView<float> HLevel::view<float>() const {
   v.dim = lev->dim;
   v.inv_h2 = (float)(1.0 / (lev->dx * lev->dx));
   v.gamma = (float)(2.0 * lev->dim / (lev->dx * lev->dx));
+  v.tile_brick = lev->tile_brick.get();
+  v.tile_start = lev->tile_start.get();
+  v.erec = lev->erec.get();
+  v.efr = lev->efr32.get();
+  v.ew64 = lev->ew64.get();
+  v.ntiles_B = lev->ntiles_B;
+  v.ntiles = lev->ntiles;
+  v.nbr = lev->nbr.get();
   return v;
 }
 template <> Work<double>& HLevel::work<double>() { return w64; }
@@ -127,14 +146,14 @@ template <> const double* HLevel::dA<double>() const { return dA64.get(); }
 template <> const float* HLevel::dA<float>() const { return dA32.get(); }
 
 template <typename T>
-static TransferView<T> tview(const Transfer& t, const Level& src, int dim);
+static TransferView<T> tview(const Transfer& t, int dim);
 template <>
-TransferView<double> tview<double>(const Transfer& t, const Level& src, int dim) {
-  return TransferView<double>{t.base.get(), t.fr64.get(), t.n, src.view(), dim};
+TransferView<double> tview<double>(const Transfer& t, int dim) {
+  return TransferView<double>{t.src_idx.get(), t.fr64.get(), t.n, dim};
 }
 template <>
-TransferView<float> tview<float>(const Transfer& t, const Level& src, int dim) {
-  return TransferView<float>{t.base.get(), t.fr32.get(), t.n, src.view(), dim};
+TransferView<float> tview<float>(const Transfer& t, int dim) {
+  return TransferView<float>{t.src_idx.get(), t.fr32.get(), t.n, dim};
 }
 
 }  // namespace cpm
@@ -245,11 +264,11 @@ static void vcycle_level(cpm_hier_s* H, int l, const T* f, T* u, cudaStream_t st
   Work<T>& cw = cv.work<T>();
   smooth<T>(H, l, f, u, H->opts.nu1, st);
   transfer_residual<T>(H, l, f, u, w.r.get(), st);
-  launch_transfer<T>(tview<T>(lv.R, *lv.lev, lv.lev->dim), w.r.get(), cw.f.get(), false, st);
+  launch_transfer<T>(tview<T>(lv.R, lv.lev->dim), w.r.get(), cw.f.get(), false, st);
   if (l + 1 < nl - 1)
     CPM_CUDA_TRY(cudaMemsetAsync(cw.u.get(), 0, sizeof(T) * cv.lev->nB, st));
   vcycle_level<T>(H, l + 1, cw.f.get(), cw.u.get(), st);
-  launch_transfer<T>(tview<T>(lv.P, *cv.lev, lv.lev->dim), cw.u.get(), u, true, st);
+  launch_transfer<T>(tview<T>(lv.P, lv.lev->dim), cw.u.get(), u, true, st);
   smooth<T>(H, l, f, u, H->opts.nu2, st);
 }
 
@@ -411,16 +430,19 @@ static void copy_level(const Level& a, Level& b, cudaStream_t st) {
   cp(b.map, a.map); cp(b.bmask, a.bmask); cp(b.gmask, a.gmask); cp(b.bstart, a.bstart);
   cp(b.gstart, a.gstart); cp(b.bcoord, a.bcoord); cp(b.key, a.key); cp(b.cp, a.cp);
   cp(b.fr64, a.fr64); cp(b.fr32, a.fr32);
+  b.ntiles_B = a.ntiles_B; b.ntiles = a.ntiles;
+  cp(b.tile_brick, a.tile_brick); cp(b.tile_start, a.tile_start); cp(b.erec, a.erec);
+  cp(b.efr32, a.efr32); cp(b.ew64, a.ew64); cp(b.nbr, a.nbr);
 }
 
 static void build_transfer(const Level& target, const Level& src, Transfer& t, cudaStream_t st,
                            int32_t* err) {
   t.n = target.nB;
-  t.base.alloc(t.n);
+  t.src_idx.alloc((size_t)(target.dim == 3 ? 8 : 4) * t.n);
   t.fr64.alloc((size_t)target.dim * t.n);
   t.fr32.alloc((size_t)target.dim * t.n);
   k_transfer_records<<<nblk(t.n, 256), 256, 0, st>>>(target.cp.get(), target.nplus(), t.n, target.dim,
-                                                     src.lo, src.dx, src.view(), t.base.get(),
+                                                     src.lo, src.dx, src.view(), t.src_idx.get(),
                                                      t.fr64.get(), t.fr32.get(), err);
   CPM_CUDA_TRY(cudaGetLastError());
 }
@@ -496,7 +518,7 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
       HLevel& a = H->L[l];
       HLevel& b = H->L[l + 1];
       b.c64.alloc(b.lev->nB);
-      launch_transfer<double>(tview<double>(a.R, *a.lev, a.lev->dim), a.c64.get(), b.c64.get(), false, st);
+      launch_transfer<double>(tview<double>(a.R, a.lev->dim), a.c64.get(), b.c64.get(), false, st);
     }
     for (auto& lv : H->L) {
       lv.c32.alloc(lv.lev->nB);
@@ -510,13 +532,14 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
     launch_diag_M(lv.view<double>(), dM.get(), st);
     lv.dA64.alloc(nB);
     lv.dA32.alloc(nB);
-    k_diag_A<<<nblk(nB, 256), 256, 0, st>>>(dM.get(), lv.c64.get(), H->c, lv.dA64.get(),
+    k_diag_A<<<nblk(nB, 256), 256, 0, st>>>(dM.get(), lv.c64.get(), H->c, o.omega, lv.dA64.get(),
                                             lv.dA32.get(), nB);
     CPM_CUDA_TRY(cudaGetLastError());
     CPM_CUDA_TRY(cudaStreamSynchronize(st));
     lv.w64.alloc(nB, np);
     lv.w32.alloc(nB, np);
   }
+  init_coarse_gemv();
   // coarsest: dense A = diag(c) - M, inverted in place (FP64)
   H->nc = cl.nB;
   if (H->coarse_sweeps == 0) {

@@ -36,57 +36,6 @@ __device__ __forceinline__ void cubic_w(T s, T w[4]) {
   w[3] = (a * sp1) * T(1.0 / 6.0);
 }
 
-// ----------------------------------------------------------------- extension
-template <typename T, int DIM>
-__global__ void __launch_bounds__(256) k_extend(LevelView<T> L, const T* __restrict__ u,
-                                                T* __restrict__ w, int32_t npts) {
-  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= npts) return;
-  const uint64_t k = __ldg(L.key + i);
-  const int bx = key_x(k) + key_ox(k);
-  const int by = key_y(k) + key_oy(k);
-  const int bz = key_z(k) + key_oz(k);
-  T wx[4], wy[4], wz[4];
-  cubic_w(__ldg(L.fr + i), wx);
-  cubic_w(__ldg(L.fr + L.nplus + i), wy);
-  if (DIM == 3) cubic_w(__ldg(L.fr + 2 * L.nplus + i), wz);
-  T acc = T(0);
-#pragma unroll
-  for (int c = 0; c < (DIM == 3 ? 4 : 1); ++c) {
-    T accy = T(0);
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const int y = by + b, z = DIM == 3 ? bz + c : 0;
-      int32_t idx = band_index(L.bv, bx, y, z);
-      idx = idx < 0 ? 0 : idx;
-      T accx = wx[0] * __ldg(u + idx);
-#pragma unroll
-      for (int a = 1; a < 4; ++a) {
-        if (((bx + a) & 3) == 0) {
-          idx = band_index(L.bv, bx + a, y, z);
-          idx = idx < 0 ? 0 : idx;
-        } else {
-          ++idx;
-        }
-        accx += wx[a] * __ldg(u + idx);
-      }
-      accy += wy[b] * accx;
-    }
-    acc += (DIM == 3 ? wz[c] : T(1)) * accy;
-  }
-  w[i] = acc;
-}
-
-template <typename T>
-void launch_extend(const LevelView<T>& L, const T* u, T* w, int32_t npts, cudaStream_t st) {
-  if (npts <= 0) return;
-  if (L.dim == 3)
-    k_extend<T, 3><<<nblk(npts, 256), 256, 0, st>>>(L, u, w, npts);
-  else
-    k_extend<T, 2><<<nblk(npts, 256), 256, 0, st>>>(L, u, w, npts);
-  count_launch();
-}
-
 // ----------------------------------------------------------------- block reduce
 __device__ inline void block_max_sum(double m, double s, double* part) {
   __shared__ double sm[32], ss[32];
@@ -123,17 +72,10 @@ __global__ void __launch_bounds__(256) k_lap(LevelView<T> L, const T* u, const T
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   double rm = 0.0, rs = 0.0;
   if (i < L.nB) {
-    const uint64_t k = __ldg(L.key + i);
-    const int x = key_x(k), y = key_y(k), z = key_z(k);
     const T wi = w[i];
-    const int nb[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
     T s = T(0);
 #pragma unroll
-    for (int q = 0; q < 2 * DIM; ++q) {
-      int32_t j = node_index(L.bv, x + nb[q][0], y + nb[q][1], z + nb[q][2]);
-      j = j < 0 ? i : j;
-      s += w[j] - wi;
-    }
+    for (int q = 0; q < 2 * DIM; ++q) s += w[__ldg(L.nbr + (int64_t)q * L.nB + i)] - wi;
     const T ui = u[i];
     const T Mu = s * L.inv_h2 + L.gamma * (wi - ui);
     if (MODE == LAP_APPLY) {
@@ -146,7 +88,7 @@ __global__ void __launch_bounds__(256) k_lap(LevelView<T> L, const T* u, const T
         rm = fabs((double)r);
         rs = (double)r * (double)r;
       } else {
-        u_inout[i] = ui + omega * r / dA[i];
+        u_inout[i] = ui + r * dA[i];
       }
     }
   }
@@ -186,14 +128,11 @@ __global__ void __launch_bounds__(256) k_rm(LevelView<T> L, const T* __restrict_
                                             T cval, T omega, T* __restrict__ out) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= L.nB) return;
-  const uint64_t k = __ldg(L.key + i);
-  const int x = key_x(k), y = key_y(k), z = key_z(k);
   T s = T(0);
-  const int d[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
 #pragma unroll
   for (int q = 0; q < 2 * DIM; ++q) {
-    const int32_t j = band_index(L.bv, x + d[q][0], y + d[q][1], z + d[q][2]);
-    if (j >= 0) s += u[j];
+    const int32_t j = __ldg(L.nbr + (int64_t)q * L.nB + i);
+    if (j < L.nB) s += u[j];  // band-restricted Laplacian: ghost neighbours dropped
   }
   const T c = cvec ? cvec[i] : cval;
   const T diag = c + L.gamma;
@@ -223,8 +162,6 @@ __global__ void __launch_bounds__(256) k_transfer(TransferView<T> tv, const T* _
                                                   T* __restrict__ dst, bool add) {
   const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= tv.n) return;
-  const uint64_t b = __ldg(tv.base + j);
-  const int bx = key_x(b), by = key_y(b), bz = key_z(b);
   const T sx = __ldg(tv.fr + j), sy = __ldg(tv.fr + tv.n + j);
   const T sz = DIM == 3 ? __ldg(tv.fr + 2 * tv.n + j) : T(0);
   const T wx[2] = {T(1) - sx, sx}, wy[2] = {T(1) - sy, sy}, wz[2] = {T(1) - sz, sz};
@@ -234,11 +171,10 @@ __global__ void __launch_bounds__(256) k_transfer(TransferView<T> tv, const T* _
     T accy = T(0);
 #pragma unroll
     for (int bb = 0; bb < 2; ++bb) {
-      int32_t i0 = band_index(tv.src, bx, by + bb, bz + c);
-      int32_t i1 = band_index(tv.src, bx + 1, by + bb, bz + c);
-      i0 = i0 < 0 ? 0 : i0;
-      i1 = i1 < 0 ? 0 : i1;
-      accy += wy[bb] * (wx[0] * __ldg(src + i0) + wx[1] * __ldg(src + i1));
+      const int q = 4 * c + 2 * bb;
+      const T v0 = __ldg(src + __ldg(tv.src_idx + (int64_t)q * tv.n + j));
+      const T v1 = __ldg(src + __ldg(tv.src_idx + (int64_t)(q + 1) * tv.n + j));
+      accy += wy[bb] * (wx[0] * v0 + wx[1] * v1);
     }
     acc += (DIM == 3 ? wz[c] : T(1)) * accy;
   }
@@ -351,25 +287,38 @@ void launch_cast_from_f64(const double* x, T* y, int64_t n, cudaStream_t st) {
 }
 
 // ----------------------------------------------------------------- coarse solve
-// x = Ainv b: one warp per row, FP64 accumulation.
+// x = Ainv b: b staged once per CTA in shared memory as FP64, one warp per
+// row, FP64 accumulation.
+constexpr int kGemvThreads = 512;
 template <typename T>
-__global__ void __launch_bounds__(256) k_coarse_gemv(const double* __restrict__ Ainv,
-                                                     const T* __restrict__ b, T* __restrict__ x,
-                                                     int32_t n) {
+__global__ void __launch_bounds__(kGemvThreads) k_coarse_gemv(const double* __restrict__ Ainv,
+                                                              const T* __restrict__ b,
+                                                              T* __restrict__ x, int32_t n) {
+  extern __shared__ double sb[];
+  for (int32_t j = threadIdx.x; j < n; j += blockDim.x) sb[j] = (double)b[j];
+  __syncthreads();
   const int32_t row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   const int lane = threadIdx.x & 31;
   if (row >= n) return;
   const double* a = Ainv + (size_t)row * n;
   double s = 0.0;
-  for (int32_t j = lane; j < n; j += 32) s += a[j] * (double)__ldg(b + j);
+  for (int32_t j = lane; j < n; j += 32) s += __ldg(a + j) * sb[j];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
   if (lane == 0) x[row] = (T)s;
 }
 
+void init_coarse_gemv() {
+  CPM_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    16384 * 8));
+  CPM_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    16384 * 8));
+}
+
 template <typename T>
 void launch_coarse_gemv(const double* Ainv, const T* b, T* x, int32_t n, cudaStream_t st) {
-  k_coarse_gemv<T><<<nblk((int64_t)n * 32, 256), 256, 0, st>>>(Ainv, b, x, n);
+  const size_t smem = (size_t)n * sizeof(double);
+  k_coarse_gemv<T><<<nblk((int64_t)n * 32, kGemvThreads), kGemvThreads, smem, st>>>(Ainv, b, x, n);
   count_launch();
 }
 
@@ -550,7 +499,6 @@ void invert_dense(double* A, int32_t n, cudaStream_t st, int32_t* err) {
 
 // ----------------------------------------------------------------- instantiations
 #define CPM_INST(T)                                                                              \
-  template void launch_extend<T>(const LevelView<T>&, const T*, T*, int32_t, cudaStream_t);      \
   template void launch_lap<T>(const LevelView<T>&, LapMode, const T*, const T*, const T*,        \
                               const T*, T, const T*, T, T*, T*, double*, int, cudaStream_t);      \
   template void launch_rm_jacobi<T>(const LevelView<T>&, const T*, const T*, const T*, T, T, T*, \

@@ -11,22 +11,29 @@ template <typename T>
 struct LevelView {
   BrickView bv;
   const uint64_t* key;  // B+ keys
-  const T* fr;          // d x nplus fractions (SoA)
+  const T* fr;          // d x nplus fractions (SoA, band order)
   int64_t nplus;
   int32_t nB;
   int dim;
   T inv_h2;   // 1/dx^2
   T gamma;    // 2d/dx^2
+  // extension tiles (ext.cu)
+  const uint32_t* tile_brick;
+  const int32_t* tile_start;
+  const uint32_t* erec;
+  const float* efr;     // E-order FP32 fractions
+  const double* ew64;   // E-order FP64 weights
+  int32_t ntiles_B, ntiles;
+  const int32_t* nbr;   // 2d x nB neighbour indices into B+
 };
 
 // Transfer records: for each target point, the base node of its linear
 // (2^d) stencil in the source grid and the fractions (SoA, d x n).
 template <typename T>
 struct TransferView {
-  const uint64_t* base;  // x | y << 16 | z << 32
+  const int32_t* src_idx;  // 2^d x n band indices of the stencil nodes in the source level
   const T* fr;
-  int32_t n;             // number of target points
-  BrickView src;         // source level bricks
+  int32_t n;               // number of target points
   int dim;
 };
 
@@ -40,7 +47,7 @@ void launch_extend(const LevelView<T>& L, const T* u, T* w, int32_t npts, cudaSt
 //   APPLY : out = M u
 //   RESID : out = f - c u + M u  (and block partials of max|out|, sum out^2
 //           into part[2*block], part[2*block+1] if part != nullptr)
-//   JACOBI: u += omega (f - c u + M u) / dA   (in place, out unused)
+//   JACOBI: u += (f - c u + M u) * wdA, wdA = omega / dA (in place, out unused)
 template <typename T>
 void launch_lap(const LevelView<T>& L, LapMode mode, const T* u, const T* w, const T* f,
                 const T* cvec, T cval, const T* dA, T omega, T* out, T* u_inout, double* part,
@@ -77,7 +84,9 @@ void launch_cast_to_f64(const T* x, double* y, int64_t n, cudaStream_t st);
 template <typename T>
 void launch_cast_from_f64(const double* x, T* y, int64_t n, cudaStream_t st);
 
-// Coarsest direct solve x = Ainv b (FP64 matrix, FP64 accumulation).
+// Coarsest direct solve x = Ainv b (FP64 matrix, FP64 accumulation);
+// init_coarse_gemv() raises the kernel's shared-memory limit (once, at setup).
+void init_coarse_gemv();
 template <typename T>
 void launch_coarse_gemv(const double* Ainv, const T* b, T* x, int32_t n, cudaStream_t st);
 
