@@ -188,7 +188,8 @@ def run_cpm(args, world, rank, local):
     pkg.build()
     t0 = time.perf_counter()
     band = pkg.Band("sphere", (), DX)
-    H = pkg.Hierarchy(band, coarsest_dx=1 / 8, nu1=3, nu2=3, omega=0.8)
+    H = pkg.Hierarchy(band, coarsest_dx=1 / 8, nu1=args.nu, nu2=args.nu, omega=args.omega,
+                      residual=args.residual)
     setup_s = time.perf_counter() - t0
     _, cp, _ = band.export()
     _, f_np = synth.sphere_harmonics(cp[: band.nb])
@@ -298,7 +299,8 @@ def run_cpm(args, world, rank, local):
         "config": {"workload": f"unit sphere dx=1/256 ({nb} band points, {band.ng} ghost), "
                                "23 N(0,1) harmonics l in {2,3,5}, c=1, tol 1e-10, mixed FP32 V-cycle "
                                "in FP64 defect correction",
-                   "levels": sizes, "smoother": "jacobi nu=3/3 omega=0.8", "transfers": "linear",
+                   "levels": sizes, "smoother": f"jacobi nu={args.nu}/{args.nu} omega={args.omega}",
+                   "residual": args.residual, "inner_cycles": args.inner, "transfers": "linear",
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "iters_mixed": iters_mixed, "fp64_s": f64_ms / 1e3, "iters_fp64": reps64[-1]["iters"],
@@ -373,6 +375,10 @@ def main():
     ap.add_argument("--impl", default="cpm", choices=["cpm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--inner", type=int, default=1, help="FP32 V-cycles per outer iteration")
+    ap.add_argument("--residual", default="extended", choices=["extended", "plain"],
+                    help="residual restricted in the V-cycle: f - A(E u) (Sec. 4.4) or f - A u")
+    ap.add_argument("--nu", type=int, default=3, help="pre- and post-smoothing sweeps")
+    ap.add_argument("--omega", type=float, default=0.8, help="Jacobi weight")
     ap.add_argument("--micro", default=None,
                     help="kernel micro-benchmark instead of the solve: extend32|extend64|apply32|apply64|all")
     args = ap.parse_args()

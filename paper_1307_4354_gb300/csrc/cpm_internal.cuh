@@ -156,6 +156,7 @@ struct Level {
   // holds their cubic stencil base ("E order"); see ext.cu
   int32_t ntiles_B = 0, ntiles = 0;
   DBuf<uint32_t> tile_brick;  // packed brick coordinates of each tile
+  DBuf<uint32_t> tile_box;    // per axis: lowest and highest base position in the brick
   DBuf<int32_t> tile_start;   // ntiles + 1 offsets into the E-order arrays
   DBuf<uint32_t> erec;        // band index << 6 | stencil base inside the brick
   DBuf<float> efr32;          // d x (nB+nG) fractions in E order

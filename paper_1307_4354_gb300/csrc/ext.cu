@@ -20,7 +20,8 @@ static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // ----------------------------------------------------------------- tile build
 __global__ void k_tile_slots(BrickView v, const uint64_t* key, int64_t nplus, int32_t nB,
-                             int32_t nbricks, int dim, int32_t* slot, int64_t* count, int32_t* err) {
+                             int32_t nbricks, int dim, int32_t* slot, int64_t* count, int32_t* err,
+                             int32_t* bbox) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nplus) return;
   const uint64_t k = key[i];
@@ -37,6 +38,11 @@ __global__ void k_tile_slots(BrickView v, const uint64_t* key, int64_t nplus, in
   const int32_t s = (i < nB ? 0 : nbricks) + b;
   slot[i] = s;
   atomicAdd(reinterpret_cast<unsigned long long*>(count + s), 1ull);
+  // bounding box of the stencil bases inside the brick: bits (min, max) per axis
+  const int l[3] = {bx & 3, by & 3, bz & 3};
+  int32_t bits = 0;
+  for (int a = 0; a < 3; ++a) bits |= (1 << l[a]) << (4 * a);
+  atomicOr(bbox + s, bits);
 }
 
 __global__ void k_tile_flags(const int64_t* count, int64_t n, int64_t* flag) {
@@ -45,13 +51,21 @@ __global__ void k_tile_flags(const int64_t* count, int64_t n, int64_t* flag) {
 }
 
 __global__ void k_tile_emit(const int64_t* count, const int64_t* offset, const int64_t* tpos,
-                            const uint32_t* bcoord, int64_t n, int32_t nbricks, uint32_t* tile_brick,
-                            int32_t* tile_start) {
+                            const uint32_t* bcoord, const int32_t* bbox, int64_t n, int32_t nbricks,
+                            uint32_t* tile_brick, uint32_t* tile_box, int32_t* tile_start) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || count[s] == 0) return;
   const int64_t t = tpos[s];
   tile_brick[t] = bcoord[s % nbricks];
   tile_start[t] = (int32_t)offset[s];
+  // packed per axis: lowest and highest base position used (2 bits each)
+  uint32_t packed = 0;
+  for (int a = 0; a < 3; ++a) {
+    const uint32_t m = (uint32_t)(bbox[s] >> (4 * a)) & 15u;
+    const uint32_t lo = __ffs(m) - 1, hi = 31 - __clz(m);
+    packed |= (lo | (hi << 2)) << (4 * a);
+  }
+  tile_box[t] = packed;
 }
 
 __global__ void k_tile_scatter(const uint64_t* key, const int32_t* slot, const int64_t* offset,
@@ -86,12 +100,13 @@ void build_ext_tiles(Level& L, cudaStream_t st) {
   const int64_t nslots = 2 * (int64_t)L.nbricks;
   DBuf<int32_t> slot(np);
   DBuf<int64_t> count(nslots), offset(nslots), cursor(nslots), tpos(nslots);
-  DBuf<int32_t> err(1);
+  DBuf<int32_t> err(1), bbox(nslots);
+  CPM_CUDA_TRY(cudaMemsetAsync(bbox.get(), 0, nslots * sizeof(int32_t), st));
   CPM_CUDA_TRY(cudaMemsetAsync(count.get(), 0, nslots * sizeof(int64_t), st));
   CPM_CUDA_TRY(cudaMemsetAsync(cursor.get(), 0, nslots * sizeof(int64_t), st));
   CPM_CUDA_TRY(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), st));
   k_tile_slots<<<nblk(np, 256), 256, 0, st>>>(L.view(), L.key.get(), np, L.nB, L.nbricks, L.dim,
-                                              slot.get(), count.get(), err.get());
+                                              slot.get(), count.get(), err.get(), bbox.get());
   CPM_CUDA_TRY(cudaGetLastError());
   CPM_CUDA_TRY(cudaMemcpyAsync(offset.get(), count.get(), nslots * sizeof(int64_t),
                                cudaMemcpyDeviceToDevice, st));
@@ -112,9 +127,11 @@ void build_ext_tiles(Level& L, cudaStream_t st) {
   L.ntiles = (int32_t)ntiles;
   L.ntiles_B = (int32_t)ntB;
   L.tile_brick.alloc(ntiles);
+  L.tile_box.alloc(ntiles);
   L.tile_start.alloc(ntiles + 1);
   k_tile_emit<<<nblk(nslots, 256), 256, 0, st>>>(count.get(), offset.get(), tpos.get(),
-                                                 L.bcoord.get(), nslots, L.nbricks, L.tile_brick.get(),
+                                                 L.bcoord.get(), bbox.get(), nslots, L.nbricks,
+                                                 L.tile_brick.get(), L.tile_box.get(),
                                                  L.tile_start.get());
   const int32_t npi = (int32_t)np;
   CPM_CUDA_TRY(cudaMemcpyAsync(L.tile_start.get() + ntiles, &npi, sizeof(int32_t),
@@ -177,18 +194,28 @@ __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, co
     sm_start[j] = b >= 0 ? __ldg(L.bv.bstart + b) : 0;
   }
   __syncthreads();
-  // stage the 7^d box: node (x, y, z) of the box feeds the windows x0 = x-3..x
-  for (int q = threadIdx.x; q < NROWS * 7; q += kExtThreads) {
-    const int x = q % 7, row = q / 7;
-    const int y = row % 7, z = row / 7;
-    const int j = (x >> 2) | ((y >> 2) << 1) | ((z >> 2) << 2);
-    const uint64_t m = sm_mask[j];
-    const uint64_t bit = 1ull << ((x & 3) | ((y & 3) << 2) | ((z & 3) << 4));
-    const T v = (m & bit) ? __ldg(u + sm_start[j] + __popcll(m & (bit - 1))) : T(0);
-#pragma unroll
-    for (int x0 = 0; x0 < 4; ++x0) {
-      const int e = x - x0;
-      if (e >= 0 && e < 4) win[row][x0][e] = v;
+  // stage the part of the 7^d box the tile's stencils use: bases span
+  // [lo, hi] per axis, so nodes lo .. hi+3.  Thread (x, y) walks z; node x
+  // feeds the windows x0 = max(lo_x, x-3) .. min(hi_x, x).
+  const uint32_t tbox = __ldg(L.tile_box + tile);
+  const int xlo = tbox & 3, xhi = (tbox >> 2) & 3;
+  const int ylo = (tbox >> 4) & 3, yhi = (tbox >> 6) & 3;
+  const int zlo = DIM == 3 ? (tbox >> 8) & 3 : 0, zhi = DIM == 3 ? (tbox >> 10) & 3 : 0;
+  {
+    const int x = xlo + (threadIdx.x & 7), y = ylo + (threadIdx.x >> 3);
+    if (x <= xhi + 3 && y <= yhi + 3) {
+      const int jxy = (x >> 2) | ((y >> 2) << 1);
+      const int lxy = (x & 3) | ((y & 3) << 2);
+      const int x0a = max(xlo, x - 3), x0b = min(xhi, x);
+      const int zend = DIM == 3 ? zhi + 3 : 0;
+      for (int z = zlo; z <= zend; ++z) {
+        const int j = jxy | ((z >> 2) << 2);
+        const uint64_t m = sm_mask[j];
+        const uint64_t bit = 1ull << (lxy | ((z & 3) << 4));
+        const T v = (m & bit) ? __ldg(u + sm_start[j] + __popcll(m & (bit - 1))) : T(0);
+        T* row = &win[z * 7 + y][0][0];
+        for (int x0 = x0a; x0 <= x0b; ++x0) row[x0 * 4 + (x - x0)] = v;
+      }
     }
   }
   __syncthreads();

@@ -19,6 +19,7 @@ struct LevelView {
   T gamma;    // 2d/dx^2
   // extension tiles (ext.cu)
   const uint32_t* tile_brick;
+  const uint32_t* tile_box;
   const int32_t* tile_start;
   const uint32_t* erec;
   const float* efr;     // E-order FP32 fractions
