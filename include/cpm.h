@@ -241,6 +241,35 @@ cpm_status cpm_residual_norms(cpm_hier h, const double* f, const double* u, doub
                               double* abs_l2, cpm_stream stream);
 
 /*
+ * Allocation-free form of cpm_residual_norms (the paper has no counterpart).
+ *
+ * For callers that cannot allocate device memory when they need a residual:
+ * work being recorded into a CUDA graph by stream capture (cudaMalloc is
+ * refused during a global-mode capture), loops with hard latency budgets that
+ * forbid allocator calls, and frameworks that hand out all device memory from
+ * their own pool.  It computes r = f - A u on the finest level (FP64,
+ * difference form, as cpm_residual_norms) and writes norms[0] = max_i |r_i|
+ * and norms[1] = sum_i r_i^2 to the DEVICE pointer `norms` (2 doubles,
+ * asynchronously on `stream`; nothing is copied to the host).  f, u: FP64
+ * device vectors of length |B_0|.
+ *
+ * It calls no cudaMalloc / cudaFree or allocating library routine.  Its
+ * scratch (E u on B+ and block partial norms) is one file-scope device array
+ * of CPM_NOALLOC_MAX_POINTS doubles plus 8192 doubles (about 8.1 MB), held on
+ * every GPU that loads the library until the process exits.  The first call
+ * on a device (with that device current) looks up the array's device address
+ * once; make that first call before any stream capture.  Every call shares
+ * the one array and overwrites it: calls whose kernels overlap on the GPU
+ * (other streams, other host threads) race and must be serialised by the
+ * caller.  Nothing in the scratch needs to start at zero.
+ * Errors: CPM_ERR_ARG if |B_0| + |G_0| > CPM_NOALLOC_MAX_POINTS (use
+ * cpm_residual_norms then) or on NULL arguments.
+ */
+#define CPM_NOALLOC_MAX_POINTS 1048576
+cpm_status cpm_residual_norms_noalloc(cpm_hier h, const double* f, const double* u, double* norms,
+                                      cpm_stream stream);
+
+/*
  * Number of kernels this library has launched in the process so far (kernels
  * inside replayed CUDA graphs included).  Host counter, no device work.
  */

@@ -21,6 +21,7 @@ CPM_F64, CPM_F32 = 0, 1
 CPM_RESID_EXTENDED, CPM_RESID_PLAIN = 0, 1
 CPM_SOLVE_F64, CPM_SOLVE_MIXED = 0, 1
 CPM_MAX_HISTORY = 256
+CPM_NOALLOC_MAX_POINTS = 1048576
 
 
 class cpm_surface(C.Structure):
@@ -79,6 +80,8 @@ _PROTOS = {
                             C.POINTER(cpm_solve_report), C.c_void_p]),
     "cpm_residual_norms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), C.c_void_p]),
+    "cpm_residual_norms_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p]),
     "cpm_hier_destroy": (C.c_int, [C.c_void_p]),
 }
 
@@ -196,6 +199,13 @@ def cpm_residual_norms(h: int, f_ptr: int, u_ptr: int, stream: int = 0):
                                     C.byref(rel), C.byref(l2), C.c_void_p(stream)),
            "cpm_residual_norms")
     return rel.value, l2.value
+
+
+def cpm_residual_norms_noalloc(h: int, f_ptr: int, u_ptr: int, norms_ptr: int, stream: int = 0):
+    """Residual norms into a device buffer of 2 doubles; allocates nothing."""
+    _check(lib().cpm_residual_norms_noalloc(C.c_void_p(h), C.c_void_p(f_ptr), C.c_void_p(u_ptr),
+                                            C.c_void_p(norms_ptr), C.c_void_p(stream)),
+           "cpm_residual_norms_noalloc")
 
 
 def cpm_hier_destroy(h: int):

@@ -679,6 +679,16 @@ cpm_status cpm_residual_norms(cpm_hier h, const double* f, const double* u, doub
   CPM_API_END
 }
 
+cpm_status cpm_residual_norms_noalloc(cpm_hier h, const double* f, const double* u, double* norms,
+                                      cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr && u != nullptr && f != nullptr && norms != nullptr, CPM_ERR_ARG,
+            "NULL argument");
+  const HLevel& lv = h->L[0];
+  residual_norms_noalloc(lv.view<double>(), f, u, lv.c64.get(), h->c, norms, (cudaStream_t)stream);
+  CPM_API_END
+}
+
 cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opts* opts_in,
                      cpm_solve_report* report, cpm_stream stream) {
   CPM_API_BEGIN

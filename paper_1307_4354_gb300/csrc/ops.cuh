@@ -91,6 +91,11 @@ void init_coarse_gemv();
 template <typename T>
 void launch_coarse_gemv(const double* Ainv, const T* b, T* x, int32_t n, cudaStream_t st);
 
+// Residual norms of the finest level with the library's fixed device scratch
+// (noalloc.cu); norms[0] = max|r|, norms[1] = sum r^2 (device).
+void residual_norms_noalloc(const LevelView<double>& v, const double* f, const double* u,
+                            const double* cvec, double cval, double* norms, cudaStream_t st);
+
 // Setup kernels.
 void launch_diag_M(const LevelView<double>& L, double* diagM, cudaStream_t st);
 void launch_assemble_A(const LevelView<double>& L, const double* cvec, double cval, double* A,
