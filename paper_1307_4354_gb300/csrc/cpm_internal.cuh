@@ -157,6 +157,8 @@ struct Level {
   int32_t ntiles_B = 0, ntiles = 0;
   DBuf<uint32_t> tile_brick;  // packed brick coordinates of each tile
   DBuf<uint32_t> tile_box;    // per axis: lowest and highest base position in the brick
+  DBuf<uint64_t> tile_mask;   // 8 per tile: band masks of the bricks the tile's box overlaps
+  DBuf<int32_t> tile_bstart;  // 8 per tile: their band starts
   DBuf<int32_t> tile_start;   // ntiles + 1 offsets into the E-order arrays
   DBuf<uint32_t> erec;        // band index << 6 | stencil base inside the brick
   DBuf<float> efr32;          // d x (nB+nG) fractions in E order

@@ -94,6 +94,33 @@ __global__ void k_tile_scatter(const uint64_t* key, const int32_t* slot, const i
   }
 }
 
+// Occupancy masks and band starts of the 2^d bricks each tile's box overlaps
+// (brick (tbx + (j & 1), tby + (j >> 1 & 1), tbz + (j >> 2)) for j < 2^d).
+__global__ void k_tile_tables(BrickView v, const uint32_t* tile_brick, int32_t ntiles, int dim,
+                              uint64_t* tmask, int32_t* tstart) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int nbr = dim == 3 ? 8 : 4;
+  if (q >= (int64_t)ntiles * 8) return;
+  const int32_t t = (int32_t)(q >> 3);
+  const int j = (int)(q & 7);
+  uint64_t m = 0;
+  int32_t s0 = 0;
+  if (j < nbr) {
+    const uint32_t tb = tile_brick[t];
+    const int bx = (int)(tb & 1023) + (j & 1), by = (int)((tb >> 10) & 1023) + ((j >> 1) & 1);
+    const int bz = dim == 3 ? (int)((tb >> 20) & 1023) + (j >> 2) : 0;
+    if (bx < v.nbx && by < v.nby && bz < v.nbz) {
+      const int32_t b = v.map[((size_t)bz * v.nby + by) * v.nbx + bx];
+      if (b >= 0) {
+        m = v.bmask[b];
+        s0 = v.bstart[b];
+      }
+    }
+  }
+  tmask[q] = m;
+  tstart[q] = s0;
+}
+
 void build_ext_tiles(Level& L, cudaStream_t st) {
   const int64_t np = L.nplus();
   CPM_CHECK(np < (1ll << 26), CPM_ERR_ARG, "more than 2^26 points on one level");
@@ -136,6 +163,11 @@ void build_ext_tiles(Level& L, cudaStream_t st) {
   const int32_t npi = (int32_t)np;
   CPM_CUDA_TRY(cudaMemcpyAsync(L.tile_start.get() + ntiles, &npi, sizeof(int32_t),
                                cudaMemcpyHostToDevice, st));
+  L.tile_mask.alloc((size_t)8 * ntiles);
+  L.tile_bstart.alloc((size_t)8 * ntiles);
+  k_tile_tables<<<nblk((int64_t)8 * ntiles, 256), 256, 0, st>>>(L.view(), L.tile_brick.get(),
+                                                                (int32_t)ntiles, L.dim,
+                                                                L.tile_mask.get(), L.tile_bstart.get());
   L.erec.alloc(np);
   L.efr32.alloc((size_t)L.dim * np);
   L.ew64.alloc((size_t)4 * L.dim * np);
@@ -168,85 +200,118 @@ __device__ __forceinline__ T dot4(const T w[4], const T* v) {
   return w[0] * v[0] + w[1] * v[1] + w[2] * v[2] + w[3] * v[3];
 }
 
-// One CTA per tile.  Shared memory: NZ*7 rows x 4 windows x 4 values.
+// Cubic weights of one point: FP64 from the precomputed E-order table, FP32
+// from the fraction (closed forms of the proof of Theorem 3.3).
+template <typename T, int DIM>
+struct PointWeights;
+template <int DIM>
+struct PointWeights<double, DIM> {
+  double wx[4], wy[4], wz[4];
+  __device__ __forceinline__ void load(const LevelView<double>& L, int32_t k) {
+    const int64_t np = L.nplus;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      wx[j] = __ldg(L.ew64 + j * np + k);
+      wy[j] = __ldg(L.ew64 + (4 + j) * np + k);
+      wz[j] = DIM == 3 ? __ldg(L.ew64 + (8 + j) * np + k) : 0.0;
+    }
+  }
+};
+template <int DIM>
+struct PointWeights<float, DIM> {
+  float wx[4], wy[4], wz[4];
+  __device__ __forceinline__ static void cubic(float s, float w[4]) {
+    const float sm1 = s - 1.f, sm2 = s - 2.f, sp1 = s + 1.f;
+    const float p = s * sm1, q = sp1 * sm2;
+    w[0] = (p * sm2) * (-1.f / 6.f);
+    w[1] = (q * sm1) * 0.5f;
+    w[2] = (q * s) * -0.5f;
+    w[3] = (p * sp1) * (1.f / 6.f);
+  }
+  __device__ __forceinline__ void load(const LevelView<float>& L, int32_t k) {
+    const int64_t np = L.nplus;
+    cubic(__ldg(L.efr + k), wx);
+    cubic(__ldg(L.efr + np + k), wy);
+    if (DIM == 3) cubic(__ldg(L.efr + 2 * np + k), wz);
+  }
+};
+
+// One CTA per tile.  Shared memory: NZ*7 box rows, each 4 windows of 4
+// values plus one pad window (row stride 20 values spreads rows over banks).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, const T* __restrict__ u,
                                                               T* __restrict__ w) {
   constexpr int NZ = DIM == 3 ? 7 : 1;
-  constexpr int NROWS = NZ * 7;
+  constexpr int RS = 20;
   constexpr int NB = DIM == 3 ? 8 : 4;  // bricks overlapping the box
-  // row stride 5 windows (one pad window) spreads the rows over the banks
-  __shared__ __align__(16) T win[NROWS][5][4];
-  __shared__ uint64_t sm_mask[NB];
-  __shared__ int32_t sm_start[NB];
+  __shared__ __align__(16) T win[NZ * 7 * RS];
+  __shared__ uint32_t sm_mask[NB][2];
+  __shared__ int32_t sm_start[NB][2];
   const int32_t tile = blockIdx.x;
-  const uint32_t tb = __ldg(L.tile_brick + tile);
-  const int tbx = (int)(tb & 1023), tby = (int)((tb >> 10) & 1023);
-  const int tbz = DIM == 3 ? (int)((tb >> 20) & 1023) : 0;
-  // occupancy masks and band starts of the 2^d bricks the box overlaps
+  const uint32_t tbox = __ldg(L.tile_box + tile);
+  const int32_t beg = __ldg(L.tile_start + tile), end = __ldg(L.tile_start + tile + 1);
+  // this thread's first point: issue its record loads before staging
+  int32_t k = beg + threadIdx.x;
+  uint32_t rec = 0;
+  PointWeights<T, DIM> pw;
+  if (k < end) {
+    rec = __ldg(L.erec + k);
+    pw.load(L, k);
+  }
+  // occupancy masks (as 32-bit halves) and band starts of the 2^d bricks
   if (threadIdx.x < NB) {
     const int j = threadIdx.x;
-    const int bx = tbx + (j & 1), by = tby + ((j >> 1) & 1), bz = tbz + (j >> 2);
-    int32_t b = -1;
-    if (bx < L.bv.nbx && by < L.bv.nby && bz < L.bv.nbz)
-      b = __ldg(L.bv.map + ((size_t)bz * L.bv.nby + by) * L.bv.nbx + bx);
-    sm_mask[j] = b >= 0 ? __ldg(L.bv.bmask + b) : 0ull;
-    sm_start[j] = b >= 0 ? __ldg(L.bv.bstart + b) : 0;
+    const uint64_t m = __ldg(L.tile_mask + 8 * (int64_t)tile + j);
+    const int32_t s0 = __ldg(L.tile_bstart + 8 * (int64_t)tile + j);
+    sm_mask[j][0] = (uint32_t)m;
+    sm_mask[j][1] = (uint32_t)(m >> 32);
+    sm_start[j][0] = s0;
+    sm_start[j][1] = s0 + __popc((uint32_t)m);
   }
   __syncthreads();
-  // stage the part of the 7^d box the tile's stencils use: bases span
-  // [lo, hi] per axis, so nodes lo .. hi+3.  Thread (x, y) walks z; node x
-  // feeds the windows x0 = max(lo_x, x-3) .. min(hi_x, x).
-  const uint32_t tbox = __ldg(L.tile_box + tile);
-  const int xlo = tbox & 3, xhi = (tbox >> 2) & 3;
-  const int ylo = (tbox >> 4) & 3, yhi = (tbox >> 6) & 3;
-  const int zlo = DIM == 3 ? (tbox >> 8) & 3 : 0, zhi = DIM == 3 ? (tbox >> 10) & 3 : 0;
+  // stage the nodes the tile's stencils read: bases span [lo, hi] per axis,
+  // so box nodes lo .. hi+3.  Thread (x, y) walks z; node x feeds windows
+  // x0 = max(lo_x, x-3) .. min(hi_x, x), at offset 3*x0 + x in its row.
   {
+    const int xlo = tbox & 3, xhi = (tbox >> 2) & 3;
+    const int ylo = (tbox >> 4) & 3, yhi = (tbox >> 6) & 3;
+    const int zlo = DIM == 3 ? (tbox >> 8) & 3 : 0, zhi = DIM == 3 ? ((tbox >> 10) & 3) + 3 : 0;
     const int x = xlo + (threadIdx.x & 7), y = ylo + (threadIdx.x >> 3);
     if (x <= xhi + 3 && y <= yhi + 3) {
       const int jxy = (x >> 2) | ((y >> 2) << 1);
-      const int lxy = (x & 3) | ((y & 3) << 2);
+      const uint32_t lbit = 1u << ((x & 3) | ((y & 3) << 2));
       const int x0a = max(xlo, x - 3), x0b = min(xhi, x);
-      const int zend = DIM == 3 ? zhi + 3 : 0;
-      for (int z = zlo; z <= zend; ++z) {
-        const int j = jxy | ((z >> 2) << 2);
-        const uint64_t m = sm_mask[j];
-        const uint64_t bit = 1ull << (lxy | ((z & 3) << 4));
-        const T v = (m & bit) ? __ldg(u + sm_start[j] + __popcll(m & (bit - 1))) : T(0);
-        T* row = &win[z * 7 + y][0][0];
-        for (int x0 = x0a; x0 <= x0b; ++x0) row[x0 * 4 + (x - x0)] = v;
+      const bool p0 = x0a <= 0 && 0 <= x0b, p1 = x0a <= 1 && 1 <= x0b;
+      const bool p2 = x0a <= 2 && 2 <= x0b, p3 = x0a <= 3 && 3 <= x0b;
+      // all loads of the column first, then the shared-memory stores
+      T v[NZ];
+#pragma unroll
+      for (int dz = 0; dz < NZ; ++dz) {
+        const int z = zlo + dz;
+        v[dz] = T(0);
+        if (z <= zhi) {
+          const int j = jxy | ((z >> 2) << 2);
+          const int half = (z >> 1) & 1;
+          const uint32_t m = sm_mask[j][half];
+          const uint32_t bit = lbit << ((z & 1) << 4);
+          if (m & bit) v[dz] = __ldg(u + sm_start[j][half] + __popc(m & (bit - 1)));
+        }
+      }
+      T* row = win + (zlo * 7 + y) * RS + x;
+#pragma unroll
+      for (int dz = 0; dz < NZ; ++dz, row += 7 * RS) {
+        if (zlo + dz <= zhi) {
+          if (p0) row[0] = v[dz];
+          if (p1) row[3] = v[dz];
+          if (p2) row[6] = v[dz];
+          if (p3) row[9] = v[dz];
+        }
       }
     }
   }
   __syncthreads();
-  const int32_t beg = __ldg(L.tile_start + tile), end = __ldg(L.tile_start + tile + 1);
-  const int64_t np = L.nplus;
-  for (int32_t k = beg + threadIdx.x; k < end; k += kExtThreads) {
-    const uint32_t rec = __ldg(L.erec + k);
-    const int lx = rec & 3, ly = (rec >> 2) & 3, lz = (rec >> 4) & 3;
-    T wx[4], wy[4], wz[4];
-    if constexpr (sizeof(T) == 8) {
-#pragma unroll
-      for (int j = 0; j < 4; ++j) {
-        wx[j] = __ldg(L.ew64 + j * np + k);
-        wy[j] = __ldg(L.ew64 + (4 + j) * np + k);
-        if (DIM == 3) wz[j] = __ldg(L.ew64 + (8 + j) * np + k);
-      }
-    } else {
-      const float sx = __ldg(L.efr + k), sy = __ldg(L.efr + np + k);
-      const float sz = DIM == 3 ? __ldg(L.efr + 2 * np + k) : 0.f;
-      const float s3[3] = {sx, sy, sz};
-      float* ws[3] = {wx, wy, wz};
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) {
-        const float s = s3[a], sm1 = s - 1.f, sm2 = s - 2.f, sp1 = s + 1.f;
-        const float p = s * sm1, q = sp1 * sm2;
-        ws[a][0] = -(p * sm2) * (1.f / 6.f);
-        ws[a][1] = (q * sm1) * 0.5f;
-        ws[a][2] = -(q * s) * 0.5f;
-        ws[a][3] = (p * sp1) * (1.f / 6.f);
-      }
-    }
+  for (; k < end; k += kExtThreads) {
+    const T* base = win + ((rec >> 4) & 3) * 7 * RS + ((rec >> 2) & 3) * RS + (rec & 3) * 4;
     T acc = T(0);
 #pragma unroll
     for (int c = 0; c < (DIM == 3 ? 4 : 1); ++c) {
@@ -254,12 +319,17 @@ __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, co
 #pragma unroll
       for (int b = 0; b < 4; ++b) {
         T vv[4];
-        load4(&win[(lz + c) * 7 + ly + b][lx][0], vv);
-        accy += wy[b] * dot4(wx, vv);
+        load4(base + (c * 7 + b) * RS, vv);
+        accy += pw.wy[b] * dot4(pw.wx, vv);
       }
-      acc += (DIM == 3 ? wz[c] : T(1)) * accy;
+      acc += (DIM == 3 ? pw.wz[c] : T(1)) * accy;
     }
     w[rec >> 6] = acc;
+    const int32_t kn = k + kExtThreads;
+    if (kn < end) {
+      rec = __ldg(L.erec + kn);
+      pw.load(L, kn);
+    }
   }
 }
 

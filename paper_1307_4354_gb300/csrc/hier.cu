@@ -109,6 +109,8 @@ LevelView<double> HLevel::view<double>() const {
   v.gamma = 2.0 * lev->dim / (lev->dx * lev->dx);
   v.tile_brick = lev->tile_brick.get();
   v.tile_box = lev->tile_box.get();
+  v.tile_mask = lev->tile_mask.get();
+  v.tile_bstart = lev->tile_bstart.get();
   v.tile_start = lev->tile_start.get();
   v.erec = lev->erec.get();
   v.efr = lev->efr32.get();
@@ -131,6 +133,8 @@ LevelView<float> HLevel::view<float>() const {
   v.gamma = (float)(2.0 * lev->dim / (lev->dx * lev->dx));
   v.tile_brick = lev->tile_brick.get();
   v.tile_box = lev->tile_box.get();
+  v.tile_mask = lev->tile_mask.get();
+  v.tile_bstart = lev->tile_bstart.get();
   v.tile_start = lev->tile_start.get();
   v.erec = lev->erec.get();
   v.efr = lev->efr32.get();
@@ -433,7 +437,7 @@ static void copy_level(const Level& a, Level& b, cudaStream_t st) {
   cp(b.gstart, a.gstart); cp(b.bcoord, a.bcoord); cp(b.key, a.key); cp(b.cp, a.cp);
   cp(b.fr64, a.fr64); cp(b.fr32, a.fr32);
   b.ntiles_B = a.ntiles_B; b.ntiles = a.ntiles;
-  cp(b.tile_brick, a.tile_brick); cp(b.tile_box, a.tile_box); cp(b.tile_start, a.tile_start); cp(b.erec, a.erec);
+  cp(b.tile_brick, a.tile_brick); cp(b.tile_box, a.tile_box); cp(b.tile_mask, a.tile_mask); cp(b.tile_bstart, a.tile_bstart); cp(b.tile_start, a.tile_start); cp(b.erec, a.erec);
   cp(b.efr32, a.efr32); cp(b.ew64, a.ew64); cp(b.nbr, a.nbr);
 }
 

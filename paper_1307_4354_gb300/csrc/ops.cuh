@@ -20,6 +20,8 @@ struct LevelView {
   // extension tiles (ext.cu)
   const uint32_t* tile_brick;
   const uint32_t* tile_box;
+  const uint64_t* tile_mask;
+  const int32_t* tile_bstart;
   const int32_t* tile_start;
   const uint32_t* erec;
   const float* efr;     // E-order FP32 fractions
