@@ -39,6 +39,27 @@ EXTEND32_BYTES = 28
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (profiling recipe table)
 
 
+def _sphere_rhs(y):
+    import synth
+    return synth.sphere_harmonics(y)[1]
+
+
+def _mixed_rhs(y):
+    import synth
+    return synth.mixed_rhs(y)
+
+
+# sphere256 is the headline; the others are the mixed-precision workloads at dx = 1/512
+WORKLOADS = {
+    "sphere256": {"kind": "sphere", "params": (), "dx": 1 / 256, "coarsest": 1 / 8, "rhs": _sphere_rhs,
+                  "desc": "unit sphere dx=1/256, 23 N(0,1) harmonics l in {2,3,5}"},
+    "sphere512": {"kind": "sphere", "params": (), "dx": 1 / 512, "coarsest": 1 / 8, "rhs": _mixed_rhs,
+                  "desc": "unit sphere dx=1/512, f = (1 + 0.5 x y) u_rand"},
+    "torus512": {"kind": "torus", "params": (1.0, 0.4), "dx": 1 / 512, "coarsest": 1 / 16,
+                 "rhs": _mixed_rhs, "desc": "torus R=1 r=0.4 dx=1/512, f = (1 + 0.5 x y) u_rand"},
+}
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -187,12 +208,13 @@ def run_cpm(args, world, rank, local):
     dev = torch.device("cuda", local)
     pkg.build()
     t0 = time.perf_counter()
-    band = pkg.Band("sphere", (), DX)
-    H = pkg.Hierarchy(band, coarsest_dx=1 / 8, nu1=args.nu, nu2=args.nu, omega=args.omega,
+    wl = WORKLOADS[args.workload]
+    band = pkg.Band(wl["kind"], wl["params"], wl["dx"])
+    H = pkg.Hierarchy(band, coarsest_dx=wl["coarsest"], nu1=args.nu, nu2=args.nu, omega=args.omega,
                       residual=args.residual)
     setup_s = time.perf_counter() - t0
     _, cp, _ = band.export()
-    _, f_np = synth.sphere_harmonics(cp[: band.nb])
+    f_np = wl["rhs"](cp[: band.nb])
     nb = band.nb
     f = torch.from_numpy(f_np).to(dev)
     u = torch.zeros(nb, dtype=torch.float64, device=dev)
@@ -240,6 +262,64 @@ def run_cpm(args, world, rank, local):
     torch.cuda.synchronize()
     f64_ms = ev0.elapsed_time(ev1) / k64
 
+    # learned smoother: trained on the GPU (own kernels) on V-cycle residuals of
+    # seeded ellipsoids and tori at dx = 1/64, then judged against Jacobi
+    learned = None
+    if not args.no_learned and args.workload == "sphere256":
+        from paper_1307_4354_gb300 import train as tr
+        t0 = time.perf_counter()
+        sets = [tr.residual_fields(kind, prm, 1 / 64, seed=i)
+                for i, (kind, prm) in enumerate(tr.training_surfaces(0, 3, 2))]
+        sm = pkg.Smoother(0)
+        for h, _ in sets:
+            h.set_smoother(sm)
+        loss0 = tr.mean_loss(sets)
+        tr.train(sm, sets, steps=args.train_steps, lr=2e-3)
+        loss1 = tr.mean_loss(sets)
+        train_s = time.perf_counter() - t0
+        del sets
+        H.set_smoother(sm)
+
+        def solve_learned():
+            _, rep = H.solve(f, u, tol=1e-10, max_iter=200, mode="mixed", zero_init=True,
+                             inner_cycles=args.inner, learned=True)
+            assert rep["converged"], rep
+            return rep
+
+        for _ in range(2):
+            solve_learned()
+        torch.cuda.synchronize()
+        ev0.record(st)
+        repsL = [solve_learned() for _ in range(args.steps)]
+        ev1.record(st)
+        torch.cuda.synchronize()
+        learned_ms = ev0.elapsed_time(ev1) / args.steps
+        # held-out evaluation: torus R = 1, r = 0.35, dx = 1/256, c = 1 + 0.5 sin(2 pi z)
+        Ht, _ = tr.residual_fields("torus", (1.0, 0.35), DX, seed=7, iters=(0,),
+                                   c_fn=lambda y: 1.0 + 0.5 * np.sin(2 * np.pi * y[:, 2]))
+        Ht.set_smoother(sm)
+        ut = torch.zeros_like(Ht._f)
+        ev = {}
+        for name, flag in (("jacobi", False), ("learned", True)):
+            Ht.solve(Ht._f, ut, tol=1e-10, max_iter=200, mode="mixed", zero_init=True,
+                     inner_cycles=args.inner, learned=flag)
+            torch.cuda.synchronize()
+            ev0.record(st)
+            _, rp = Ht.solve(Ht._f, ut, tol=1e-10, max_iter=200, mode="mixed", zero_init=True,
+                             inner_cycles=args.inner, learned=flag)
+            ev1.record(st)
+            torch.cuda.synchronize()
+            ev[name] = {"s": ev0.elapsed_time(ev1) / 1e3, "iters": rp["iters"],
+                        "converged": rp["converged"], "fallback": rp["fallback"],
+                        "jacobi_factor": rp["jacobi_factor"], "learned_factor": rp["learned_factor"]}
+        learned = {"s": learned_ms / 1e3, "iters": repsL[-1]["iters"],
+                   "fallback": repsL[-1]["fallback"], "jacobi_factor": repsL[-1]["jacobi_factor"],
+                   "learned_factor": repsL[-1]["learned_factor"], "train_s": train_s,
+                   "train_steps": args.train_steps, "train_loss": [loss0, loss1],
+                   "torus_r035_dx256_variable_c": ev, "torus_points": Ht.nb}
+        H.set_smoother(None)
+        del Ht
+
     # end to end through the C ABI with host buffers
     f_host = torch.from_numpy(f_np).pin_memory()
     u_host = torch.empty(nb, dtype=torch.float64).pin_memory()
@@ -286,7 +366,8 @@ def run_cpm(args, world, rank, local):
 
     if rank != 0:
         return
-    cpu = oracle_sample(steps=1, warmup=0) if not args.no_cpu_baseline else None
+    cpu = (oracle_sample(steps=1, warmup=0)
+           if not args.no_cpu_baseline and args.workload == "sphere256" else None)
     nl = H.n_levels
     sizes = [H.level_size(l) for l in range(nl)]
     sweeps = 6
@@ -296,14 +377,14 @@ def run_cpm(args, world, rank, local):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed_ms,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"unit sphere dx=1/256 ({nb} band points, {band.ng} ghost), "
-                               "23 N(0,1) harmonics l in {2,3,5}, c=1, tol 1e-10, mixed FP32 V-cycle "
-                               "in FP64 defect correction",
+        "config": {"workload": f"{wl['desc']} ({nb} band points, {band.ng} ghost), c=1, tol 1e-10, "
+                               "mixed FP32 V-cycle in FP64 defect correction",
                    "levels": sizes, "smoother": f"jacobi nu={args.nu}/{args.nu} omega={args.omega}",
                    "residual": args.residual, "inner_cycles": args.inner, "transfers": "linear",
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "iters_mixed": iters_mixed, "fp64_s": f64_ms / 1e3, "iters_fp64": reps64[-1]["iters"],
+        "learned": learned,
         "band_point_updates_per_s": updates / (mixed_ms * 1e-3),
         "setup_s": setup_s,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": nb * 8,
@@ -374,10 +455,13 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cpm", choices=["cpm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--inner", type=int, default=1, help="FP32 V-cycles per outer iteration")
-    ap.add_argument("--residual", default="extended", choices=["extended", "plain"],
+    ap.add_argument("--inner", type=int, default=2, help="FP32 V-cycles per outer iteration")
+    ap.add_argument("--residual", default="plain", choices=["extended", "plain"],
                     help="residual restricted in the V-cycle: f - A(E u) (Sec. 4.4) or f - A u")
     ap.add_argument("--nu", type=int, default=3, help="pre- and post-smoothing sweeps")
+    ap.add_argument("--no-learned", action="store_true", help="skip the learned-smoother form")
+    ap.add_argument("--workload", default="sphere256", choices=sorted(WORKLOADS))
+    ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--omega", type=float, default=0.8, help="Jacobi weight")
     ap.add_argument("--micro", default=None,
                     help="kernel micro-benchmark instead of the solve: extend32|extend64|apply32|apply64|all")

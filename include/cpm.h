@@ -141,9 +141,11 @@ typedef struct cpm_mg_opts {
                              linear interpolation from the finest band          */
   int32_t residual_mode;  /* residual restricted by the Jacobi V-cycle:
                              0: f - A (E u) (Sec. 4.4), 1: f - A u              */
-  int32_t coarse_sweeps;  /* coarsest level: 0 = direct solve (explicit FP64
-                             inverse) when it has <= 16384 points, else 40
-                             Jacobi sweeps; > 0 = that many Jacobi sweeps       */
+  int32_t coarse_sweeps;  /* coarsest level: 0 = direct solve by an explicit
+                             inverse, FP64 (Gauss-Jordan) up to 16384 points,
+                             FP32 (library LU at setup, FP64 refinement in FP64
+                             V-cycles) up to 40000, else 40 Jacobi sweeps;
+                             > 0 = that many Jacobi sweeps                      */
 } cpm_mg_opts;
 
 typedef struct cpm_hier_s* cpm_hier;
@@ -196,6 +198,51 @@ cpm_status cpm_smooth(cpm_hier h, int32_t level, int32_t prec, const void* f, vo
  */
 cpm_status cpm_vcycle(cpm_hier h, int32_t prec, const void* f, void* u, cpm_stream stream);
 
+/* ------------------------------------------------------- learned smoother */
+
+/*
+ * A per-band-point network that replaces the first pre-smoothing Jacobi sweep
+ * (Eq. 4.1) on the finest level of FP32 V-cycles; weighted Jacobi is its
+ * fallback and judge (cpm_solve_opts.learned).  The paper has no learned
+ * component.  Features of band point i (31): the residual on the 3x3x3 grid
+ * neighbourhood of x_i (0 off the band) divided by its max |r| = s_i,
+ * (x_i - cp(x_i))/dx (3), dx^2 M_ii (1).  Network 31 -> 64 -> 64 -> 1 with
+ * ReLU, BF16 weights and features, FP32 accumulation on the tensor cores;
+ * correction du_i = s_i dx^2 y_i.  Parameters: CPM_MLP_NPARAMS floats, W1
+ * (32 x 64, row 31 unused), b1 (64), W2 (64 x 64), b2 (64), w3 (64), b3 (1),
+ * matrices row-major [input][output].
+ */
+#define CPM_MLP_NPARAMS 6337
+typedef struct cpm_mlp_s* cpm_mlp;
+
+/* Seeded random initialisation (He-scaled normal weights, zero biases). */
+cpm_status cpm_mlp_create(uint64_t seed, cpm_mlp* out);
+/* Copy parameters from / to HOST memory (n must be CPM_MLP_NPARAMS). */
+cpm_status cpm_mlp_set_params(cpm_mlp m, const float* params, int32_t n);
+cpm_status cpm_mlp_get_params(cpm_mlp m, float* params, int32_t n);
+cpm_status cpm_mlp_destroy(cpm_mlp m);
+
+/* Use m (NULL: none) as the learned smoother of the finest level of h. */
+cpm_status cpm_hier_set_smoother(cpm_hier h, cpm_mlp m);
+
+/* du = network correction for the FP32 residual r on the finest level
+ * (device vectors of length |B_0|).  Needs cpm_hier_set_smoother first. */
+cpm_status cpm_mlp_correction(cpm_hier h, const float* r, float* du, cpm_stream stream);
+
+/*
+ * Training loss L = ||r - A du||^2 / ||r||^2 of one FP32 residual field r on
+ * the finest level of h (A applied in FP32) and its gradient with respect to
+ * the parameters (analytic backward pass; A^T by a transposed neighbour
+ * gather and a transposed extension scatter).  loss and grad are HOST outputs
+ * (grad: CPM_MLP_NPARAMS floats, may be NULL).  Synchronous.
+ */
+cpm_status cpm_mlp_loss_grad(cpm_hier h, const float* r, double* loss, float* grad,
+                             cpm_stream stream);
+
+/* One Adam step (lr; beta1 0.9, beta2 0.999) on the loss above.  loss: host
+ * output (may be NULL; reading it synchronises). */
+cpm_status cpm_mlp_train_step(cpm_hier h, const float* r, float lr, double* loss, cpm_stream stream);
+
 typedef enum cpm_solve_mode {
   CPM_SOLVE_F64 = 0,   /* FP64 V-cycles in FP64 defect correction            */
   CPM_SOLVE_MIXED = 1  /* FP32 V-cycle preconditioning an FP64 outer loop:
@@ -212,6 +259,13 @@ typedef struct cpm_solve_opts {
   int32_t inner_cycles;/* MIXED: FP32 V-cycles per outer iteration, each after
                           the first starting from the previous correction
                           (an FP32 inner defect correction; 0: 1)             */
+  int32_t learned;     /* MIXED: 1 = use the smoother set by
+                          cpm_hier_set_smoother, judged against Jacobi: the
+                          first outer iteration runs plain Jacobi V-cycles and
+                          gives the reference reduction factor; an iteration
+                          with the network whose reduction factor exceeds
+                          1.25 x the reference switches the network off for
+                          the rest of the solve                             */
 } cpm_solve_opts;
 
 #define CPM_MAX_HISTORY 256
@@ -221,6 +275,11 @@ typedef struct cpm_solve_report {
   double rel_residual;         /* final ||f - A u||_inf / ||f||_inf            */
   double history[CPM_MAX_HISTORY]; /* relative residual before each iteration  */
   double seconds;              /* wall time of the solve (host clock)         */
+  int32_t learned_iters;       /* outer iterations that used the network      */
+  int32_t fallback;            /* 1 if the judge switched the network off     */
+  double jacobi_factor;        /* reference reduction factor (Jacobi)         */
+  double learned_factor;       /* mean reduction factor with the network      */
+  double learned_worst;        /* largest reduction factor with the network   */
 } cpm_solve_report;
 
 /*
@@ -232,6 +291,12 @@ typedef struct cpm_solve_report {
  */
 cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opts* opts,
                      cpm_solve_report* report, cpm_stream stream);
+
+/*
+ * r = f - A u on the finest level in FP64 (the outer residual of cpm_solve,
+ * difference form of M).  f, u, r: FP64 device vectors of length |B_0|.
+ */
+cpm_status cpm_residual(cpm_hier h, const double* f, const double* u, double* r, cpm_stream stream);
 
 /*
  * Relative residual ||f - A u||_inf / ||f||_inf and ||f - A u||_2 on the

@@ -41,12 +41,19 @@ class cpm_mg_opts(C.Structure):
 
 class cpm_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("mode", C.c_int32),
-                ("use_graph", C.c_int32), ("zero_init", C.c_int32), ("inner_cycles", C.c_int32)]
+                ("use_graph", C.c_int32), ("zero_init", C.c_int32), ("inner_cycles", C.c_int32),
+                ("learned", C.c_int32)]
 
 
 class cpm_solve_report(C.Structure):
     _fields_ = [("iters", C.c_int32), ("converged", C.c_int32), ("rel_residual", C.c_double),
-                ("history", C.c_double * CPM_MAX_HISTORY), ("seconds", C.c_double)]
+                ("history", C.c_double * CPM_MAX_HISTORY), ("seconds", C.c_double),
+                ("learned_iters", C.c_int32), ("fallback", C.c_int32),
+                ("jacobi_factor", C.c_double), ("learned_factor", C.c_double),
+                ("learned_worst", C.c_double)]
+
+
+CPM_MLP_NPARAMS = 6337
 
 
 class CpmError(RuntimeError):
@@ -78,11 +85,22 @@ _PROTOS = {
     "cpm_vcycle": (C.c_int, [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cpm_solve": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(cpm_solve_opts),
                             C.POINTER(cpm_solve_report), C.c_void_p]),
+    "cpm_residual": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cpm_residual_norms": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(C.c_double),
                                      C.POINTER(C.c_double), C.c_void_p]),
     "cpm_residual_norms_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                              C.c_void_p]),
     "cpm_hier_destroy": (C.c_int, [C.c_void_p]),
+    "cpm_mlp_create": (C.c_int, [C.c_uint64, C.POINTER(C.c_void_p)]),
+    "cpm_mlp_set_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "cpm_mlp_get_params": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int32]),
+    "cpm_mlp_destroy": (C.c_int, [C.c_void_p]),
+    "cpm_hier_set_smoother": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "cpm_mlp_correction": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cpm_mlp_loss_grad": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_double), C.c_void_p,
+                                    C.c_void_p]),
+    "cpm_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_float, C.POINTER(C.c_double),
+                                     C.c_void_p]),
 }
 
 
@@ -193,6 +211,11 @@ def cpm_solve(h: int, f_ptr: int, u_ptr: int, opts: cpm_solve_opts, stream: int 
     return st, rep
 
 
+def cpm_residual(h: int, f_ptr: int, u_ptr: int, r_ptr: int, stream: int = 0):
+    _check(lib().cpm_residual(C.c_void_p(h), C.c_void_p(f_ptr), C.c_void_p(u_ptr), C.c_void_p(r_ptr),
+                              C.c_void_p(stream)), "cpm_residual")
+
+
 def cpm_residual_norms(h: int, f_ptr: int, u_ptr: int, stream: int = 0):
     rel, l2 = C.c_double(), C.c_double()
     _check(lib().cpm_residual_norms(C.c_void_p(h), C.c_void_p(f_ptr), C.c_void_p(u_ptr),
@@ -210,3 +233,45 @@ def cpm_residual_norms_noalloc(h: int, f_ptr: int, u_ptr: int, norms_ptr: int, s
 
 def cpm_hier_destroy(h: int):
     _check(lib().cpm_hier_destroy(C.c_void_p(h)), "cpm_hier_destroy")
+
+
+def cpm_mlp_create(seed: int = 0) -> int:
+    out = C.c_void_p()
+    _check(lib().cpm_mlp_create(seed, C.byref(out)), "cpm_mlp_create")
+    return out.value
+
+
+def cpm_mlp_set_params(m: int, params_ptr: int, n: int = CPM_MLP_NPARAMS):
+    _check(lib().cpm_mlp_set_params(C.c_void_p(m), C.c_void_p(params_ptr), n), "cpm_mlp_set_params")
+
+
+def cpm_mlp_get_params(m: int, params_ptr: int, n: int = CPM_MLP_NPARAMS):
+    _check(lib().cpm_mlp_get_params(C.c_void_p(m), C.c_void_p(params_ptr), n), "cpm_mlp_get_params")
+
+
+def cpm_mlp_destroy(m: int):
+    _check(lib().cpm_mlp_destroy(C.c_void_p(m)), "cpm_mlp_destroy")
+
+
+def cpm_hier_set_smoother(h: int, m: int | None):
+    _check(lib().cpm_hier_set_smoother(C.c_void_p(h), C.c_void_p(m)), "cpm_hier_set_smoother")
+
+
+def cpm_mlp_correction(h: int, r_ptr: int, du_ptr: int, stream: int = 0):
+    _check(lib().cpm_mlp_correction(C.c_void_p(h), C.c_void_p(r_ptr), C.c_void_p(du_ptr),
+                                    C.c_void_p(stream)), "cpm_mlp_correction")
+
+
+def cpm_mlp_loss_grad(h: int, r_ptr: int, grad_ptr: int | None, stream: int = 0) -> float:
+    loss = C.c_double()
+    _check(lib().cpm_mlp_loss_grad(C.c_void_p(h), C.c_void_p(r_ptr), C.byref(loss),
+                                   C.c_void_p(grad_ptr), C.c_void_p(stream)), "cpm_mlp_loss_grad")
+    return loss.value
+
+
+def cpm_mlp_train_step(h: int, r_ptr: int, lr: float, stream: int = 0, want_loss: bool = True):
+    loss = C.c_double()
+    _check(lib().cpm_mlp_train_step(C.c_void_p(h), C.c_void_p(r_ptr), C.c_float(lr),
+                                    C.byref(loss) if want_loss else None, C.c_void_p(stream)),
+           "cpm_mlp_train_step")
+    return loss.value if want_loss else None

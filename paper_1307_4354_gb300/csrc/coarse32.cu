@@ -1,0 +1,105 @@
+// Coarsest-level solve for levels too large for the FP64 Gauss-Jordan inverse
+// (tori and thin ellipsoids stop coarsening at a few 10^4 points, Sec. 4.3's
+// bands must stay inside the reach).  At setup the dense matrix
+// A_c = diag(c) - M_c is assembled in FP32 and inverted once with a library LU
+// (cuSOLVER getrf / getrs on the identity; setup only).  Each V-cycle then
+// applies the explicit inverse with the GEMV below; FP64 V-cycles add two
+// steps of iterative refinement with the FP64 residual (hier.cu).
+#include <cusolverDn.h>
+
+#include "ops.cuh"
+
+namespace cpm {
+
+static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+#define CPM_SOLVER_TRY(expr)                                                              \
+  do {                                                                                    \
+    cusolverStatus_t s_ = (expr);                                                         \
+    if (s_ != CUSOLVER_STATUS_SUCCESS)                                                    \
+      throw ::cpm::Error{CPM_ERR_CUDA, std::string(#expr) + ": cusolver status " +        \
+                                           std::to_string((int)s_)};                      \
+  } while (0)
+
+__global__ void k_identity(float* X, int64_t n) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n * n) X[q] = (q / n == q % n) ? 1.f : 0.f;
+}
+
+__global__ void k_check_info(const int* info, int32_t* err) {
+  if (threadIdx.x == 0 && blockIdx.x == 0 && info[0] != 0) atomicOr(err, 1);
+}
+
+// A: row-major n x n FP32 (overwritten by its LU); X: receives A^-1 (row-major).
+// Row-major A read as column-major is A^T; solving A^T Y = I column-major
+// gives Y = A^-T, whose column-major storage is A^-1 row-major.
+void invert_dense_f32(float* A, float* X, int32_t n, cudaStream_t st, int32_t* err) {
+  cusolverDnHandle_t h = nullptr;
+  CPM_SOLVER_TRY(cusolverDnCreate(&h));
+  struct Guard {
+    cusolverDnHandle_t h;
+    ~Guard() { cusolverDnDestroy(h); }
+  } guard{h};
+  CPM_SOLVER_TRY(cusolverDnSetStream(h, st));
+  int lwork = 0;
+  CPM_SOLVER_TRY(cusolverDnSgetrf_bufferSize(h, n, n, A, n, &lwork));
+  DBuf<float> work(lwork > 0 ? lwork : 1);
+  DBuf<int> ipiv(n), info(1);
+  CPM_SOLVER_TRY(cusolverDnSgetrf(h, n, n, A, n, work.get(), ipiv.get(), info.get()));
+  k_check_info<<<1, 32, 0, st>>>(info.get(), err);
+  k_identity<<<nblk((int64_t)n * n, 256), 256, 0, st>>>(X, n);
+  CPM_SOLVER_TRY(cusolverDnSgetrs(h, CUBLAS_OP_N, n, n, A, n, ipiv.get(), X, n, info.get()));
+  k_check_info<<<1, 32, 0, st>>>(info.get(), err);
+  CPM_CUDA_TRY(cudaGetLastError());
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+}
+
+// x (+)= Ainv b with an FP32 matrix: b staged in shared memory as FP32, one
+// warp per row, FP32 accumulation.
+constexpr int kGemv32Threads = 512;
+template <typename T, bool ADD>
+__global__ void __launch_bounds__(kGemv32Threads) k_coarse_gemv32(const float* __restrict__ Ainv,
+                                                                  const T* __restrict__ b,
+                                                                  T* __restrict__ x, int32_t n) {
+  extern __shared__ float sb32[];
+  for (int32_t j = threadIdx.x; j < n; j += blockDim.x) sb32[j] = (float)b[j];
+  __syncthreads();
+  const int32_t row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= n) return;
+  const float* a = Ainv + (size_t)row * n;
+  float s = 0.f;
+  for (int32_t j = lane; j < n; j += 32) s += __ldg(a + j) * sb32[j];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) x[row] = ADD ? x[row] + (T)s : (T)s;
+}
+
+void init_coarse_gemv32() {
+  CPM_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv32<double, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CPM_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv32<double, true>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+  CPM_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv32<float, false>,
+                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+}
+
+template <typename T>
+void launch_coarse_gemv32(const float* Ainv, const T* b, T* x, int32_t n, bool add, cudaStream_t st) {
+  const size_t smem = (size_t)n * sizeof(float);
+  const unsigned grid = nblk((int64_t)n * 32, kGemv32Threads);
+  if (add) {
+    if constexpr (sizeof(T) == 8)
+      k_coarse_gemv32<T, true><<<grid, kGemv32Threads, smem, st>>>(Ainv, b, x, n);
+  } else {
+    k_coarse_gemv32<T, false><<<grid, kGemv32Threads, smem, st>>>(Ainv, b, x, n);
+  }
+  count_launch();
+}
+
+template void launch_coarse_gemv32<double>(const float*, const double*, double*, int32_t, bool,
+                                           cudaStream_t);
+template void launch_coarse_gemv32<float>(const float*, const float*, float*, int32_t, bool,
+                                          cudaStream_t);
+
+}  // namespace cpm

@@ -8,7 +8,7 @@
 #include <string>
 #include <vector>
 
-#include "ops.cuh"
+#include "mlp.cuh"
 
 namespace cpm {
 
@@ -81,6 +81,7 @@ struct HLevel {
   DBuf<float> c32;
   DBuf<double> dA64;  // omega / (c - diag(M))
   DBuf<float> dA32;
+  DBuf<double> dM64;  // diag(M)
   Transfer R;  // restriction: targets = B of level l+1, source = this level
   Transfer P;  // prolongation: targets = B of this level, source = level l+1
   Work<double> w64;
@@ -171,9 +172,11 @@ struct cpm_hier_s {
   cpm_mg_opts opts;
   double c = 1.0;
   std::vector<HLevel> L;
-  DBuf<double> Ainv;
+  DBuf<double> Ainv;     // coarse_mode 0: FP64 inverse
+  DBuf<float> Ainv32;    // coarse_mode 1: FP32 inverse
   int32_t nc = 0;
-  int32_t coarse_sweeps = 0;  // 0: direct solve with Ainv
+  int32_t coarse_mode = 0;    // 0: FP64 inverse, 1: FP32 inverse (+FP64 refinement), 2: sweeps
+  int32_t coarse_sweeps = 0;
   DBuf<double> part;   // norm partials (2 per block)
   int part_blocks = 0;
   DBuf<double> norms;  // [max, sumsq, 1/max]
@@ -182,9 +185,13 @@ struct cpm_hier_s {
   DBuf<float> r32, d32;
   cudaStream_t hs = nullptr;
   cudaEvent_t ev = nullptr;
-  cudaGraphExec_t graph[2] = {nullptr, nullptr};
-  int64_t graph_kernels[2] = {0, 0};
-  int32_t graph_inner[2] = {0, 0};
+  // graphs of one outer step: FP64, mixed, mixed with the learned smoother
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  int64_t graph_kernels[3] = {0, 0, 0};
+  int32_t graph_inner[3] = {0, 0, 0};
+  cpm_mlp mlp = nullptr;
+  std::unique_ptr<cpm::MlpLevelData> mlpd;
+  bool learned_active = false;
   double* pinned = nullptr;
   ~cpm_hier_s() {
     for (auto& g : graph)
@@ -242,8 +249,23 @@ static void transfer_residual(cpm_hier_s* H, int l, const T* f, const T* u, T* r
 template <typename T>
 static void coarse_solve(cpm_hier_s* H, const T* f, T* u, cudaStream_t st) {
   const int l = (int)H->L.size() - 1;
-  if (H->coarse_sweeps == 0) {
+  if (H->coarse_mode == 0) {
     launch_coarse_gemv<T>(H->Ainv.get(), f, u, H->nc, st);
+    return;
+  }
+  if (H->coarse_mode == 1) {
+    launch_coarse_gemv32<T>(H->Ainv32.get(), f, u, H->nc, false, st);
+    if constexpr (sizeof(T) == 8) {
+      // two steps of iterative refinement with the FP64 residual of the level
+      HLevel& lv = H->L[l];
+      const LevelView<double> v = lv.view<double>();
+      for (int it = 0; it < 2; ++it) {
+        launch_extend<double>(v, u, lv.w64.w.get(), (int32_t)v.nplus, st);
+        launch_lap<double>(v, LAP_RESID, u, lv.w64.w.get(), f, lv.c64.get(), H->c, nullptr, 0.0,
+                           lv.w64.r.get(), nullptr, nullptr, 0, st);
+        launch_coarse_gemv32<double>(H->Ainv32.get(), lv.w64.r.get(), u, H->nc, true, st);
+      }
+    }
     return;
   }
   CPM_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(T) * H->L[l].lev->nB, st));
@@ -268,7 +290,19 @@ static void vcycle_level(cpm_hier_s* H, int l, const T* f, T* u, cudaStream_t st
   HLevel& cv = H->L[l + 1];
   Work<T>& w = lv.work<T>();
   Work<T>& cw = cv.work<T>();
-  smooth<T>(H, l, f, u, H->opts.nu1, st);
+  int pre = H->opts.nu1;
+  if constexpr (sizeof(T) == 4) {
+    if (l == 0 && H->learned_active && pre > 0) {
+      // learned smoother in place of the first Jacobi sweep: r = f - A u, u += net(r)
+      const LevelView<float> v = lv.view<float>();
+      launch_extend<float>(v, u, w.w.get(), (int32_t)v.nplus, st);
+      launch_lap<float>(v, LAP_RESID, u, w.w.get(), f, lv.cvec<float>(), (float)H->c, nullptr, 0.f,
+                        w.r.get(), nullptr, nullptr, 0, st);
+      mlp_forward(H->mlp->params.get(), *H->mlpd, w.r.get(), 1.f / v.inv_h2, nullptr, u, nullptr, st);
+      --pre;
+    }
+  }
+  smooth<T>(H, l, f, u, pre, st);
   transfer_residual<T>(H, l, f, u, w.r.get(), st);
   launch_transfer<T>(tview<T>(lv.R, lv.lev->dim), w.r.get(), cw.f.get(), false, st);
   if (l + 1 < nl - 1)
@@ -506,7 +540,17 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
   const int nl = (int)H->L.size();
   const Level& cl = *H->L[nl - 1].lev;
   CPM_CHECK(o.coarse_sweeps >= 0 && o.coarse_sweeps <= 10000, CPM_ERR_ARG, "bad coarse_sweeps");
-  H->coarse_sweeps = o.coarse_sweeps > 0 ? o.coarse_sweeps : (cl.nB <= 16384 ? 0 : 40);
+  if (o.coarse_sweeps > 0) {
+    H->coarse_mode = 2;
+    H->coarse_sweeps = o.coarse_sweeps;
+  } else if (cl.nB <= 16384) {
+    H->coarse_mode = 0;
+  } else if (cl.nB <= 40000) {
+    H->coarse_mode = 1;
+  } else {
+    H->coarse_mode = 2;
+    H->coarse_sweeps = 40;
+  }
   CPM_CHECK(o.residual_mode == 0 || o.residual_mode == 1, CPM_ERR_ARG, "bad residual_mode");
 
   DBuf<int32_t> err(1);
@@ -542,18 +586,30 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
                                             lv.dA32.get(), nB);
     CPM_CUDA_TRY(cudaGetLastError());
     CPM_CUDA_TRY(cudaStreamSynchronize(st));
+    lv.dM64 = std::move(dM);
     lv.w64.alloc(nB, np);
     lv.w32.alloc(nB, np);
   }
   init_coarse_gemv();
   // coarsest: dense A = diag(c) - M, inverted in place (FP64)
   H->nc = cl.nB;
-  if (H->coarse_sweeps == 0) {
-    H->Ainv.alloc((size_t)H->nc * H->nc);
-    CPM_CUDA_TRY(cudaMemsetAsync(H->Ainv.get(), 0, sizeof(double) * (size_t)H->nc * H->nc, st));
-    launch_assemble_A(H->L[nl - 1].view<double>(), H->L[nl - 1].c64.get(), H->c, H->Ainv.get(), st);
+  const size_t nn = (size_t)H->nc * H->nc;
+  if (H->coarse_mode == 0) {
+    H->Ainv.alloc(nn);
+    CPM_CUDA_TRY(cudaMemsetAsync(H->Ainv.get(), 0, sizeof(double) * nn, st));
+    launch_assemble_A<double>(H->L[nl - 1].view<double>(), H->L[nl - 1].c64.get(), H->c,
+                              H->Ainv.get(), st);
     CPM_CUDA_TRY(cudaGetLastError());
     invert_dense(H->Ainv.get(), H->nc, st, err.get());
+  } else if (H->coarse_mode == 1) {
+    init_coarse_gemv32();
+    DBuf<float> A32(nn);
+    CPM_CUDA_TRY(cudaMemsetAsync(A32.get(), 0, sizeof(float) * nn, st));
+    launch_assemble_A<float>(H->L[nl - 1].view<double>(), H->L[nl - 1].c64.get(), H->c, A32.get(),
+                             st);
+    CPM_CUDA_TRY(cudaGetLastError());
+    H->Ainv32.alloc(nn);
+    invert_dense_f32(A32.get(), H->Ainv32.get(), H->nc, st, err.get());
   }
   int32_t herr = 0;
   CPM_CUDA_TRY(cudaMemcpyAsync(&herr, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
@@ -665,6 +721,14 @@ cpm_status cpm_vcycle(cpm_hier h, int32_t prec, const void* f, void* u, cpm_stre
   CPM_API_END
 }
 
+cpm_status cpm_residual(cpm_hier h, const double* f, const double* u, double* r, cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr && u != nullptr && f != nullptr && r != nullptr, CPM_ERR_ARG, "NULL argument");
+  outer_residual(h, f, u, r, (cudaStream_t)stream);
+  CPM_CUDA_TRY(cudaGetLastError());
+  CPM_API_END
+}
+
 cpm_status cpm_residual_norms(cpm_hier h, const double* f, const double* u, double* rel_inf,
                               double* abs_l2, cpm_stream stream) {
   CPM_API_BEGIN
@@ -725,13 +789,21 @@ cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opt
   const double fmax = h->pinned[4];
   CPM_CHECK(std::isfinite(fmax), CPM_ERR_ARG, "f is not finite");
   const double fn = fmax > 0 ? fmax : 1.0;
-  cudaGraphExec_t& gx = h->graph[o.mode];
-  if (gx && h->graph_inner[o.mode] != o.inner_cycles) {
-    cudaGraphExecDestroy(gx);
-    gx = nullptr;
-  }
-  if (o.use_graph && !gx) {
-    h->graph_inner[o.mode] = o.inner_cycles;
+  CPM_CHECK(!o.learned || (o.mode == CPM_SOLVE_MIXED && h->mlp), CPM_ERR_ARG,
+            "learned smoothing needs mode MIXED and cpm_hier_set_smoother");
+  h->learned_active = false;
+  int gi = o.mode;
+  auto graph_for = [&](int idx) -> cudaGraphExec_t& {
+    cudaGraphExec_t& g = h->graph[idx];
+    if (g && h->graph_inner[idx] != o.inner_cycles) {
+      cudaGraphExecDestroy(g);
+      g = nullptr;
+    }
+    return g;
+  };
+  auto capture = [&](int idx) {
+    cudaGraphExec_t& gx = h->graph[idx];
+    h->graph_inner[idx] = o.inner_cycles;
     cudaGraph_t g;
     CPM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
     set_capturing(true);
@@ -754,29 +826,59 @@ cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opt
       CPM_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
       nk += t == cudaGraphNodeTypeKernel;
     }
-    h->graph_kernels[o.mode] = nk;
+    h->graph_kernels[idx] = nk;
     CPM_CUDA_TRY(cudaGraphInstantiate(&gx, g, 0));
     CPM_CUDA_TRY(cudaGraphDestroy(g));
-  }
+  };
   cpm_solve_report rep{};
   double rel = h->pinned[0] / fn, best = rel;
   cpm_status result = CPM_ERR_NOT_CONVERGED;
   int it = 0;
+  // learned smoothing: iteration 0 runs plain Jacobi V-cycles and sets the
+  // reference reduction factor; later iterations use the network until one
+  // of them reduces the residual by a factor worse than 1.25 x that reference
+  // (then plain Jacobi for the rest of the solve).
+  bool learned_on = false;
+  double ref_factor = 0.0, learned_log = 0.0;
   for (;; ++it) {
     if (it < CPM_MAX_HISTORY) rep.history[it] = rel;
     if (rel <= o.tol) { result = CPM_OK; break; }
     if (!std::isfinite(rel) || rel > 1e3 * best) { result = CPM_ERR_DIVERGED; break; }
     if (it >= o.max_iter) break;
     best = std::min(best, rel);
+    if (o.learned && it == 1 && !rep.fallback) learned_on = true;
+    h->learned_active = learned_on;
+    gi = learned_on ? 2 : o.mode;
     if (o.use_graph) {
-      CPM_CUDA_TRY(cudaGraphLaunch(gx, st));
-      count_launch(h->graph_kernels[o.mode]);
-    } else
+      cudaGraphExec_t& g = graph_for(gi);
+      if (!g) capture(gi);
+      CPM_CUDA_TRY(cudaGraphLaunch(h->graph[gi], st));
+      count_launch(h->graph_kernels[gi]);
+    } else {
       outer_step(h, o.mode, o.inner_cycles, st);
+    }
     CPM_CUDA_TRY(cudaMemcpyAsync(h->pinned, h->norms.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
     CPM_CUDA_TRY(cudaStreamSynchronize(st));
+    const double prev = rel;
     rel = h->pinned[0] / fn;
+    if (o.learned) {
+      const double fac = prev > 0 ? rel / prev : 0.0;
+      if (it == 0) {
+        ref_factor = fac;
+      } else if (learned_on) {
+        ++rep.learned_iters;
+        learned_log += std::log(std::max(fac, 1e-300));
+        rep.learned_worst = std::max(rep.learned_worst, fac);
+        if (fac > 1.25 * ref_factor) {
+          learned_on = false;
+          rep.fallback = 1;
+        }
+      }
+    }
   }
+  h->learned_active = false;
+  rep.jacobi_factor = ref_factor;
+  rep.learned_factor = rep.learned_iters ? std::exp(learned_log / rep.learned_iters) : 0.0;
   CPM_CUDA_TRY(cudaMemcpyAsync(u, h->u_own.get(), nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
   CPM_CUDA_TRY(cudaEventRecord(h->ev, st));
   CPM_CUDA_TRY(cudaStreamWaitEvent(us, h->ev, 0));
@@ -789,6 +891,132 @@ cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opt
   if (result != CPM_OK) {
     cpm::set_last_error(result == CPM_ERR_DIVERGED ? "residual diverged" : "max_iter reached");
     return result;
+  }
+  CPM_API_END
+}
+
+// ----------------------------------------------------------------- learned smoother
+static double splitmix_normal(uint64_t& state) {
+  auto next = [&]() {
+    uint64_t z = (state += 0x9e3779b97f4a7c15ull);
+    z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+    z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+    return z ^ (z >> 31);
+  };
+  const double u1 = ((next() >> 11) + 1.0) * (1.0 / 9007199254740993.0);
+  const double u2 = (next() >> 11) * (1.0 / 9007199254740992.0);
+  return std::sqrt(-2.0 * std::log(u1)) * std::cos(6.283185307179586 * u2);
+}
+
+cpm_status cpm_mlp_create(uint64_t seed, cpm_mlp* out) {
+  CPM_API_BEGIN
+  CPM_CHECK(out != nullptr, CPM_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  std::unique_ptr<cpm_mlp_s> m(new cpm_mlp_s);
+  std::vector<float> p(kNParams, 0.f);
+  uint64_t st = seed;
+  for (int k = 0; k < 31; ++k)
+    for (int n = 0; n < 64; ++n) p[kOffW1 + k * 64 + n] = (float)(splitmix_normal(st) * std::sqrt(2.0 / 31));
+  for (int q = 0; q < 64 * 64; ++q) p[kOffW2 + q] = (float)(splitmix_normal(st) * std::sqrt(2.0 / 64));
+  for (int q = 0; q < 64; ++q) p[kOffW3 + q] = (float)(splitmix_normal(st) * std::sqrt(1.0 / 64));
+  m->params.alloc(kNParams);
+  m->m.alloc(kNParams);
+  m->v.alloc(kNParams);
+  CPM_CUDA_TRY(cudaMemcpy(m->params.get(), p.data(), kNParams * sizeof(float), cudaMemcpyHostToDevice));
+  CPM_CUDA_TRY(cudaMemset(m->m.get(), 0, kNParams * sizeof(float)));
+  CPM_CUDA_TRY(cudaMemset(m->v.get(), 0, kNParams * sizeof(float)));
+  *out = m.release();
+  CPM_API_END
+}
+
+cpm_status cpm_mlp_set_params(cpm_mlp m, const float* params, int32_t n) {
+  CPM_API_BEGIN
+  CPM_CHECK(m != nullptr && params != nullptr && n == kNParams, CPM_ERR_ARG, "bad arguments");
+  CPM_CUDA_TRY(cudaMemcpy(m->params.get(), params, kNParams * sizeof(float), cudaMemcpyHostToDevice));
+  CPM_CUDA_TRY(cudaMemset(m->m.get(), 0, kNParams * sizeof(float)));
+  CPM_CUDA_TRY(cudaMemset(m->v.get(), 0, kNParams * sizeof(float)));
+  m->step = 0;
+  CPM_API_END
+}
+
+cpm_status cpm_mlp_get_params(cpm_mlp m, float* params, int32_t n) {
+  CPM_API_BEGIN
+  CPM_CHECK(m != nullptr && params != nullptr && n == kNParams, CPM_ERR_ARG, "bad arguments");
+  CPM_CUDA_TRY(cudaDeviceSynchronize());
+  CPM_CUDA_TRY(cudaMemcpy(params, m->params.get(), kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+  CPM_API_END
+}
+
+cpm_status cpm_mlp_destroy(cpm_mlp m) {
+  CPM_API_BEGIN
+  delete m;
+  CPM_API_END
+}
+
+cpm_status cpm_hier_set_smoother(cpm_hier h, cpm_mlp m) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr, CPM_ERR_ARG, "hierarchy is NULL");
+  if (h->graph[2]) {
+    cudaGraphExecDestroy(h->graph[2]);
+    h->graph[2] = nullptr;
+  }
+  h->mlp = m;
+  if (m && !h->mlpd) {
+    CPM_CHECK(h->L[0].lev->dim == 3, CPM_ERR_ARG, "the learned smoother is for surfaces in 3-D");
+    h->mlpd.reset(new MlpLevelData);
+    h->mlpd->build(*h->L[0].lev, h->L[0].dM64.get(), h->hs);
+    CPM_CUDA_TRY(cudaStreamSynchronize(h->hs));
+  }
+  CPM_API_END
+}
+
+cpm_status cpm_mlp_correction(cpm_hier h, const float* r, float* du, cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr && r != nullptr && du != nullptr, CPM_ERR_ARG, "NULL argument");
+  CPM_CHECK(h->mlp && h->mlpd, CPM_ERR_ARG, "no learned smoother set (cpm_hier_set_smoother)");
+  const double dx = h->L[0].lev->dx;
+  mlp_forward(h->mlp->params.get(), *h->mlpd, r, (float)(dx * dx), du, nullptr, nullptr,
+              (cudaStream_t)stream);
+  CPM_CUDA_TRY(cudaGetLastError());
+  CPM_API_END
+}
+
+static void mlp_loss_grad_host(cpm_hier h, const float* r, cudaStream_t st) {
+  CPM_CHECK(h != nullptr && r != nullptr, CPM_ERR_ARG, "NULL argument");
+  CPM_CHECK(h->mlp && h->mlpd, CPM_ERR_ARG, "no learned smoother set (cpm_hier_set_smoother)");
+  HLevel& lv = h->L[0];
+  mlp_loss_grad(h->mlp->params.get(), *h->mlpd, lv.view<float>(), lv.c32.get(), (float)h->c, r,
+                h->mlp->tb, st);
+}
+
+cpm_status cpm_mlp_loss_grad(cpm_hier h, const float* r, double* loss, float* grad, cpm_stream stream) {
+  CPM_API_BEGIN
+  cudaStream_t st = (cudaStream_t)stream;
+  mlp_loss_grad_host(h, r, st);
+  double l2[2];
+  CPM_CUDA_TRY(cudaMemcpyAsync(l2, h->mlp->tb.loss.get(), sizeof(l2), cudaMemcpyDeviceToHost, st));
+  if (grad)
+    CPM_CUDA_TRY(cudaMemcpyAsync(grad, h->mlp->tb.grad.get(), kNParams * sizeof(float),
+                                 cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  if (loss) *loss = l2[1] > 0 ? l2[0] / l2[1] : 0.0;
+  CPM_API_END
+}
+
+cpm_status cpm_mlp_train_step(cpm_hier h, const float* r, float lr, double* loss, cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(lr > 0 && std::isfinite(lr), CPM_ERR_ARG, "lr must be positive");
+  cudaStream_t st = (cudaStream_t)stream;
+  mlp_loss_grad_host(h, r, st);
+  cpm_mlp m = h->mlp;
+  ++m->step;
+  mlp_adam(m->params.get(), m->tb.grad.get(), m->m.get(), m->v.get(), m->step, lr, st);
+  CPM_CUDA_TRY(cudaGetLastError());
+  if (loss) {
+    double l2[2];
+    CPM_CUDA_TRY(cudaMemcpyAsync(l2, m->tb.loss.get(), sizeof(l2), cudaMemcpyDeviceToHost, st));
+    CPM_CUDA_TRY(cudaStreamSynchronize(st));
+    *loss = l2[1] > 0 ? l2[0] / l2[1] : 0.0;
   }
   CPM_API_END
 }

@@ -360,13 +360,13 @@ void launch_diag_M(const LevelView<double>& L, double* diagM, cudaStream_t st) {
 // ----------------------------------------------------------------- setup: dense A
 // Row i of A = diag(c) - M: A_ii += c_i + gamma, A_ij -= E_{k,j}/dx^2 for each
 // neighbour k of i and stencil node j of cp(x_k).  One thread per row.
-template <int DIM>
-__global__ void k_assemble_A(LevelView<double> L, const double* cvec, double cval, double* A) {
+template <int DIM, typename M>
+__global__ void k_assemble_A(LevelView<double> L, const double* cvec, double cval, M* A) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   const int32_t n = L.nB;
   if (i >= n) return;
-  double* row = A + (size_t)i * n;
-  row[i] += (cvec ? cvec[i] : cval) + L.gamma;
+  M* row = A + (size_t)i * n;
+  row[i] += (M)((cvec ? cvec[i] : cval) + L.gamma);
   const uint64_t ki = L.key[i];
   const int own[3] = {key_x(ki), key_y(ki), key_z(ki)};
   const int d[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
@@ -384,16 +384,21 @@ __global__ void k_assemble_A(LevelView<double> L, const double* cvec, double cva
       for (int b = 0; b < 4; ++b)
         for (int a = 0; a < 4; ++a) {
           const int32_t j = band_index(L.bv, bx + a, by + b, DIM == 3 ? bz + c : 0);
-          if (j >= 0) row[j] -= wx[a] * wy[b] * wz[c] * L.inv_h2;
+          if (j >= 0) row[j] -= (M)(wx[a] * wy[b] * wz[c] * L.inv_h2);
         }
   }
 }
 
-void launch_assemble_A(const LevelView<double>& L, const double* cvec, double cval, double* A,
+template <typename M>
+void launch_assemble_A(const LevelView<double>& L, const double* cvec, double cval, M* A,
                        cudaStream_t st) {
-  if (L.dim == 3) k_assemble_A<3><<<nblk(L.nB, 128), 128, 0, st>>>(L, cvec, cval, A);
-  else k_assemble_A<2><<<nblk(L.nB, 128), 128, 0, st>>>(L, cvec, cval, A);
+  if (L.dim == 3) k_assemble_A<3, M><<<nblk(L.nB, 128), 128, 0, st>>>(L, cvec, cval, A);
+  else k_assemble_A<2, M><<<nblk(L.nB, 128), 128, 0, st>>>(L, cvec, cval, A);
 }
+template void launch_assemble_A<double>(const LevelView<double>&, const double*, double, double*,
+                                        cudaStream_t);
+template void launch_assemble_A<float>(const LevelView<double>&, const double*, double, float*,
+                                       cudaStream_t);
 
 // ----------------------------------------------------------------- setup: inverse
 // Gauss-Jordan with partial pivoting, in place: at step k the pivot row p

@@ -98,9 +98,17 @@ void launch_coarse_gemv(const double* Ainv, const T* b, T* x, int32_t n, cudaStr
 void residual_norms_noalloc(const LevelView<double>& v, const double* f, const double* u,
                             const double* cvec, double cval, double* norms, cudaStream_t st);
 
+// Coarsest solve with an FP32 explicit inverse (coarse32.cu): x (+)= Ainv b.
+void init_coarse_gemv32();
+template <typename T>
+void launch_coarse_gemv32(const float* Ainv, const T* b, T* x, int32_t n, bool add, cudaStream_t st);
+// A (row-major FP32, overwritten) -> X = A^-1 (library LU, setup only).
+void invert_dense_f32(float* A, float* X, int32_t n, cudaStream_t st, int32_t* err);
+
 // Setup kernels.
 void launch_diag_M(const LevelView<double>& L, double* diagM, cudaStream_t st);
-void launch_assemble_A(const LevelView<double>& L, const double* cvec, double cval, double* A,
+template <typename M>
+void launch_assemble_A(const LevelView<double>& L, const double* cvec, double cval, M* A,
                        cudaStream_t st);
 // In-place Gauss-Jordan inversion with partial pivoting (row-major n x n).
 void invert_dense(double* A, int32_t n, cudaStream_t st, int32_t* err);

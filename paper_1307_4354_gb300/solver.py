@@ -132,9 +132,39 @@ class Hierarchy:
                         _stream(stream))
         return u
 
+    def residual(self, f: torch.Tensor, u: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        """r = f - A u on the finest level (FP64)."""
+        out = torch.empty_like(f) if out is None else out
+        capi.cpm_residual(self.handle, _ptr(f, torch.float64, self.nb), _ptr(u, torch.float64, self.nb),
+                          _ptr(out, torch.float64, self.nb), _stream(stream))
+        return out
+
+    def set_smoother(self, smoother: "Smoother | None"):
+        """Use a learned smoother for the first finest-level pre-sweep of FP32 V-cycles."""
+        self._smoother = smoother
+        capi.cpm_hier_set_smoother(self.handle, smoother.handle if smoother else None)
+
+    def smoother_correction(self, r: torch.Tensor, out: torch.Tensor | None = None, stream=None):
+        out = torch.empty_like(r) if out is None else out
+        capi.cpm_mlp_correction(self.handle, _ptr(r, torch.float32, self.nb),
+                                _ptr(out, torch.float32, self.nb), _stream(stream))
+        return out
+
+    def smoother_loss_grad(self, r: torch.Tensor, stream=None):
+        grad = np.empty(capi.CPM_MLP_NPARAMS, np.float32)
+        loss = capi.cpm_mlp_loss_grad(self.handle, _ptr(r, torch.float32, self.nb), grad.ctypes.data,
+                                      _stream(stream))
+        return loss, grad
+
+    def smoother_train_step(self, r: torch.Tensor, lr: float = 1e-3, want_loss: bool = True,
+                            stream=None):
+        return capi.cpm_mlp_train_step(self.handle, _ptr(r, torch.float32, self.nb), lr,
+                                       _stream(stream), want_loss)
+
     def solve(self, f: torch.Tensor, u: torch.Tensor | None = None, tol: float = 1e-10,
               max_iter: int = 100, mode: str = "f64", use_graph: bool = True, stream=None,
-              raise_on_fail: bool = True, inner_cycles: int = 1, zero_init: bool | None = None):
+              raise_on_fail: bool = True, inner_cycles: int = 1, zero_init: bool | None = None,
+              learned: bool = False):
         zero = u is None if zero_init is None else bool(zero_init)
         if u is None:
             u = torch.empty_like(f)
@@ -143,12 +173,15 @@ class Hierarchy:
         o.mode = capi.CPM_SOLVE_MIXED if mode == "mixed" else capi.CPM_SOLVE_F64
         o.use_graph, o.zero_init = int(use_graph), int(zero)
         o.inner_cycles = inner_cycles
+        o.learned = int(learned)
         st, rep = capi.cpm_solve(self.handle, _ptr(f, torch.float64, self.nb),
                                  _ptr(u, torch.float64, self.nb), o, _stream(stream), raise_on_fail)
         n = min(rep.iters + 1, capi.CPM_MAX_HISTORY)
         return u, {"status": st, "iters": rep.iters, "converged": bool(rep.converged),
                    "rel_residual": rep.rel_residual, "history": list(rep.history[:n]),
-                   "seconds": rep.seconds}
+                   "seconds": rep.seconds, "learned_iters": rep.learned_iters,
+                   "fallback": bool(rep.fallback), "jacobi_factor": rep.jacobi_factor,
+                   "learned_factor": rep.learned_factor, "learned_worst": rep.learned_worst}
 
     def residual_norms(self, f: torch.Tensor, u: torch.Tensor, stream=None):
         return capi.cpm_residual_norms(self.handle, _ptr(f, torch.float64, self.nb),
@@ -157,6 +190,39 @@ class Hierarchy:
     def close(self):
         if getattr(self, "handle", None):
             capi.cpm_hier_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Smoother:
+    """Learned smoother network (cpm_mlp): parameters live on the device."""
+
+    def __init__(self, seed: int = 0, params: np.ndarray | None = None):
+        self.handle = capi.cpm_mlp_create(seed)
+        if params is not None:
+            self.set_params(params)
+
+    def get_params(self) -> np.ndarray:
+        out = np.empty(capi.CPM_MLP_NPARAMS, np.float32)
+        capi.cpm_mlp_get_params(self.handle, out.ctypes.data)
+        return out
+
+    def set_params(self, params: np.ndarray):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        assert p.size == capi.CPM_MLP_NPARAMS
+        capi.cpm_mlp_set_params(self.handle, p.ctypes.data)
+
+    def save(self, path: str):
+        np.save(path, self.get_params())
+
+    def close(self):
+        if getattr(self, "handle", None):
+            capi.cpm_mlp_destroy(self.handle)
             self.handle = None
 
     def __del__(self):

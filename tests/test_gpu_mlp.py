@@ -1,0 +1,89 @@
+"""Learned smoother on the GPU vs the FP64 oracle network, training and judge."""
+import numpy as np
+import pytest
+
+from helpers import oracle_surface, perm_gpu_to_oracle, require_cuda
+from oracle.band import build_band
+from oracle.mlp import MLP, correction, loss_and_grad, neighbour27
+from oracle.operators import Operators
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+def oracle_mlp(p):
+    p = np.asarray(p, dtype=np.float64)
+    return MLP(p[0:31 * 64].reshape(31, 64), p[2048:2112], p[2112:6208].reshape(64, 64),
+               p[6208:6272], p[6272:6336], float(p[6336]))
+
+
+def _pair(kind="sphere", params=(), dx=1 / 16, seed=3):
+    torch, pkg = require_cuda()
+    g = pkg.Band(kind, params, dx)
+    H = pkg.Hierarchy(g, coarsest_dx=1 / 8 if kind == "sphere" else dx * 2, coarse_sweeps=0 if kind == "sphere" else 10)
+    sm = pkg.Smoother(seed)
+    params_ = sm.get_params()
+    params_[2048:2112] += 0.1  # positive biases: more active units
+    params_[6208:6272] += 0.1
+    sm.set_params(params_)
+    H.set_smoother(sm)
+    ob = build_band(oracle_surface(kind, params), dx)
+    op = Operators(ob)
+    perm = perm_gpu_to_oracle(g, ob)
+    return torch, pkg, g, H, sm, ob, op, perm, oracle_mlp(params_)
+
+
+def test_correction_matches_oracle():
+    torch, pkg, g, H, sm, ob, op, perm, om = _pair()
+    r = synth.random_band_vector(ob.nb, 8).astype(np.float32).astype(np.float64)
+    ref, _ = correction(om, ob, r, op.diag_M())
+    got = H.smoother_correction(torch.from_numpy(r[perm]).float().cuda()).double().cpu().numpy()
+    err = np.abs(got - ref[perm]).max() / np.abs(ref).max()
+    assert err < 3e-2, err  # BF16 features and weights, FP32 accumulation
+
+
+def test_loss_and_gradient_match_oracle():
+    torch, pkg, g, H, sm, ob, op, perm, om = _pair()
+    r = synth.random_band_vector(ob.nb, 9).astype(np.float32).astype(np.float64)
+    L_ref, grads = loss_and_grad(om, ob, op.A_matrix(1.0), r, op.diag_M(), neighbour27(ob))
+    L, gp = H.smoother_loss_grad(torch.from_numpy(r[perm]).float().cuda())
+    assert abs(L - L_ref) <= 2e-2 * L_ref, (L, L_ref)
+    ref = np.zeros(6337)
+    ref[0:31 * 64] = grads[0].ravel()
+    ref[2048:2112] = grads[1]
+    ref[2112:6208] = grads[2].ravel()
+    ref[6208:6272] = grads[3]
+    ref[6272:6336] = grads[4]
+    ref[6336] = grads[5][0]
+    assert np.all(gp[31 * 64:2048] == 0)
+    for a, b in [(0, 31 * 64), (2048, 2112), (2112, 6208), (6208, 6272), (6272, 6336)]:
+        rel = np.linalg.norm(gp[a:b] - ref[a:b]) / np.linalg.norm(ref[a:b])
+        assert rel < 6e-2, (a, b, rel)
+
+
+def test_training_reduces_loss_and_solve_is_judged():
+    torch, pkg = require_cuda()
+    from paper_1307_4354_gb300 import train as tr
+    sets = [tr.residual_fields("ellipsoid", (1.1, 0.9, 0.8), 1 / 32, seed=1),
+            tr.residual_fields("torus", (1.0, 0.4), 1 / 32, seed=2)]
+    sm = pkg.Smoother(0)
+    for H, _ in sets:
+        H.set_smoother(sm)
+    before = tr.mean_loss(sets)
+    tr.train(sm, sets, steps=300, lr=2e-3)
+    after = tr.mean_loss(sets)
+    assert after < 0.8 * before, (before, after)
+    # a learned solve converges to the tolerance, judged against Jacobi
+    H, _ = tr.residual_fields("torus", (1.0, 0.35), 1 / 32, seed=5,
+                              c_fn=lambda y: 1.0 + 0.5 * np.sin(2 * np.pi * y[:, 2]))
+    H.set_smoother(sm)
+    u, rep = H.solve(H._f, tol=1e-10, mode="mixed", learned=True, max_iter=80)
+    assert rep["converged"], rep
+    assert rep["learned_iters"] >= 1 and rep["jacobi_factor"] > 0
+    if rep["fallback"]:
+        assert rep["learned_worst"] > 1.25 * rep["jacobi_factor"]
+    else:
+        assert rep["learned_worst"] <= 1.25 * rep["jacobi_factor"]
+    u2, rep2 = H.solve(H._f, tol=1e-10, mode="mixed", learned=False, max_iter=80)
+    assert rep2["converged"]
+    assert torch.abs(u - u2).max().item() <= 1e-8 * torch.abs(u2).max().item()

@@ -114,3 +114,17 @@ def test_vcycle_parity_rm_and_coarse_sweeps():
     u = torch.zeros(nb, dtype=torch.float64, device="cuda")
     H.vcycle(torch.from_numpy(synth.random_band_vector(nb, 5)[perm]).cuda(), u)
     assert np.abs(u.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+def test_vcycle_parity_large_coarsest_level():
+    """Torus: the coarsest level (dx = 1/16, ~33k points) is solved with the FP32
+    explicit inverse and two FP64 refinement steps; the V-cycle still matches the
+    oracle's (sparse LU coarsest solve)."""
+    torch, pkg, g, H, OH, perm = _hier_pair("torus", (1.0, 0.4), 1 / 32, coarsest=1 / 16)
+    nb = OH.fine.band.nb
+    assert OH.levels[-1].band.nb > 16384
+    f_o = synth.random_band_vector(nb, 12)
+    ref = vcycle(OH, np.zeros(nb), f_o)[perm]
+    u = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    H.vcycle(torch.from_numpy(f_o[perm]).cuda(), u)
+    assert np.abs(u.cpu().numpy() - ref).max() <= 1e-9 * np.abs(ref).max()
