@@ -234,7 +234,8 @@ def run_cpm(args, world, rank, local):
     # warm-up (also captures the CUDA graphs)
     for _ in range(args.warmup):
         solve("mixed")
-        solve("f64")
+        if not args.only_mixed:
+            solve("f64")
     torch.cuda.synchronize()
 
     # timed: mixed precision (headline)
@@ -253,6 +254,10 @@ def run_cpm(args, world, rank, local):
     mixed_ms = max_over_ranks(mixed_ms, world, dev)
     iters_mixed = reps[-1]["iters"]
 
+    if args.only_mixed:
+        print(json.dumps({"mixed_ms": mixed_ms, "iters": iters_mixed, "gpu_launches": int(launches)}),
+              flush=True)
+        return
     # plain FP64 solve (context)
     k64 = max(1, min(args.steps, 3))
     torch.cuda.synchronize()
@@ -461,6 +466,8 @@ def main():
     ap.add_argument("--nu", type=int, default=3, help="pre- and post-smoothing sweeps")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-smoother form")
     ap.add_argument("--workload", default="sphere256", choices=sorted(WORKLOADS))
+    ap.add_argument("--only-mixed", action="store_true",
+                    help="time only the mixed-precision solve (profiling runs)")
     ap.add_argument("--train-steps", type=int, default=400)
     ap.add_argument("--omega", type=float, default=0.8, help="Jacobi weight")
     ap.add_argument("--micro", default=None,
