@@ -298,6 +298,58 @@ cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opt
  */
 cpm_status cpm_residual(cpm_hier h, const double* f, const double* u, double* r, cpm_stream stream);
 
+/* ---------------------------------------------------------------- batches */
+
+typedef struct cpm_batch_s* cpm_batch;
+
+#define CPM_BATCH_MAX_SYSTEMS 4096
+
+/*
+ * A batch of independent systems (c - Delta_S) u = f (the problem of Sec. 2.1
+ * posed on several surfaces and with several right-hand sides, band sizes
+ * uneven): n_hier hierarchies, each with n_rhs right-hand sides; system
+ * s = i * n_rhs + k uses hierarchy i (n_hier * n_rhs <= CPM_BATCH_MAX_SYSTEMS).
+ * Every system gets its own workspace (work vectors of every level, about
+ * 130 bytes per finest band point); the hierarchies' static data is shared,
+ * not owned by the batch, and must outlive it.  tune_cache: optional path of a
+ * text file ("<batch key> <K>" per line) in which the autotuner keeps the
+ * concurrency it chose for a batch of this shape (NULL: no file).  No
+ * counterpart in the paper, which solves one system at a time.  Synchronous.
+ */
+cpm_status cpm_build_batch(const cpm_hier* hiers, int32_t n_hier, int32_t n_rhs,
+                           const char* tune_cache, cpm_batch* out);
+
+/*
+ * Solve every system of the batch with the outer loop of cpm_solve (FP64
+ * defect correction or FP32 V-cycles in FP64 iterative refinement; the
+ * learned smoother is not used in batches: CPM_ERR_ARG if opts->learned).
+ * f[s], u[s]: host arrays of n_hier * n_rhs device pointers to FP64 vectors of
+ * length |B_0| of system s's hierarchy (caller-owned); u[s] is the initial
+ * guess unless opts->zero_init.  Each outer iteration of all active systems is
+ * one launch of a CUDA graph in which the systems run on K concurrent
+ * branches, largest first; the autotuner picks K: the first outer iterations
+ * try K = 1, 2, 4, ..., min(32, systems), each a real iteration, and keep the
+ * fastest (stored in the tune cache; read from it when present).  After each
+ * launch the host reads every system's residual norm.  A system's result is
+ * its first iterate with ||f - A u||_inf / ||f||_inf <= tol (the same iterate
+ * cpm_solve returns); its workspace may keep iterating inside the graph until
+ * the graph is re-captured over the remaining systems (when they are at most
+ * half of it).  reports: n_hier * n_rhs entries or NULL (seconds = wall time
+ * of the whole batch).  Returns CPM_ERR_NOT_CONVERGED / CPM_ERR_DIVERGED if
+ * any system did (its last iterate is then in u[s]).  Synchronous.
+ */
+cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u,
+                           const cpm_solve_opts* opts, cpm_solve_report* reports, cpm_stream stream);
+
+/* Concurrency chosen by the autotuner (0 before the first solve) and the
+ * measured device time of one outer iteration (ms) for each K tried
+ * (tune_ms[q] for K = 2^q, q < 8; 0 where not tried).  Host outputs, either
+ * may be NULL. */
+cpm_status cpm_batch_info(cpm_batch b, int32_t* concurrency, double* tune_ms);
+
+/* Free the workspaces and streams of the batch (not its hierarchies). */
+cpm_status cpm_batch_destroy(cpm_batch b);
+
 /*
  * Relative residual ||f - A u||_inf / ||f||_inf and ||f - A u||_2 on the
  * finest level in FP64 (host outputs).  Synchronous.

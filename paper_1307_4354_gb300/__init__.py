@@ -6,4 +6,4 @@ handles around torch tensors.  ``build()`` compiles the library in place.
 """
 from ._build import build  # noqa: F401
 from . import capi  # noqa: F401
-from .solver import Band, Hierarchy, Smoother, make_surface  # noqa: F401
+from .solver import Band, Batch, Hierarchy, Smoother, make_surface  # noqa: F401

@@ -101,6 +101,12 @@ _PROTOS = {
                                     C.c_void_p]),
     "cpm_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_float, C.POINTER(C.c_double),
                                      C.c_void_p]),
+    "cpm_build_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_char_p,
+                                  C.POINTER(C.c_void_p)]),
+    "cpm_solve_batch": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
+                                  C.POINTER(cpm_solve_opts), C.c_void_p, C.c_void_p]),
+    "cpm_batch_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
+    "cpm_batch_destroy": (C.c_int, [C.c_void_p]),
 }
 
 
@@ -275,3 +281,35 @@ def cpm_mlp_train_step(h: int, r_ptr: int, lr: float, stream: int = 0, want_loss
                                     C.byref(loss) if want_loss else None, C.c_void_p(stream)),
            "cpm_mlp_train_step")
     return loss.value if want_loss else None
+
+
+def cpm_build_batch(hiers: list[int], n_rhs: int, tune_cache: str | None = None) -> int:
+    arr = (C.c_void_p * len(hiers))(*hiers)
+    out = C.c_void_p()
+    _check(lib().cpm_build_batch(arr, len(hiers), n_rhs,
+                                 tune_cache.encode() if tune_cache else None, C.byref(out)),
+           "cpm_build_batch")
+    return out.value
+
+
+def cpm_solve_batch(b: int, f_ptrs: list[int], u_ptrs: list[int], opts: cpm_solve_opts,
+                    stream: int = 0, raise_on_fail: bool = True):
+    n = len(f_ptrs)
+    fa = (C.c_void_p * n)(*f_ptrs)
+    ua = (C.c_void_p * n)(*u_ptrs)
+    reps = (cpm_solve_report * n)()
+    st = lib().cpm_solve_batch(C.c_void_p(b), fa, ua, C.byref(opts), reps, C.c_void_p(stream))
+    if raise_on_fail:
+        _check(st, "cpm_solve_batch")
+    return st, list(reps)
+
+
+def cpm_batch_info(b: int):
+    k = C.c_int32()
+    ms = (C.c_double * 8)()
+    _check(lib().cpm_batch_info(C.c_void_p(b), C.byref(k), ms), "cpm_batch_info")
+    return k.value, list(ms)
+
+
+def cpm_batch_destroy(b: int):
+    _check(lib().cpm_batch_destroy(C.c_void_p(b)), "cpm_batch_destroy")

@@ -121,6 +121,38 @@ __global__ void k_tile_tables(BrickView v, const uint32_t* tile_brick, int32_t n
   tstart[q] = s0;
 }
 
+// Order the points of each tile by (stencil base position, band index): points
+// with equal bases become neighbours in a warp (shared-memory broadcasts instead
+// of bank conflicts) and the E order no longer depends on atomics.  Tiles of
+// more than kSortMax points keep their order.
+constexpr int kSortMax = 4096;
+__global__ void k_tile_sort(const int32_t* tile_start, int64_t nplus, int dim, const uint32_t* erec,
+                            const float* efr32, const double* ew64, uint32_t* erec2, float* efr2,
+                            double* ew2) {
+  __shared__ uint32_t keys[kSortMax];
+  const int32_t beg = tile_start[blockIdx.x], end = tile_start[blockIdx.x + 1];
+  const int n = end - beg;
+  const bool sort = n <= kSortMax;
+  if (sort)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const uint32_t r = erec[beg + j];
+      keys[j] = ((r & 63u) << 26) | (r >> 6);
+    }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    int rank = j;
+    if (sort) {
+      const uint32_t kj = keys[j];
+      rank = 0;
+      for (int i = 0; i < n; ++i) rank += keys[i] < kj;
+    }
+    const int64_t src = beg + j, dst = beg + rank;
+    erec2[dst] = erec[src];
+    for (int a = 0; a < dim; ++a) efr2[a * nplus + dst] = efr32[a * nplus + src];
+    for (int q = 0; q < 4 * dim; ++q) ew2[q * nplus + dst] = ew64[q * nplus + src];
+  }
+}
+
 void build_ext_tiles(Level& L, cudaStream_t st) {
   const int64_t np = L.nplus();
   CPM_CHECK(np < (1ll << 26), CPM_ERR_ARG, "more than 2^26 points on one level");
@@ -175,6 +207,20 @@ void build_ext_tiles(Level& L, cudaStream_t st) {
                                                 np, L.dim, L.fr64.get(), L.erec.get(),
                                                 L.efr32.get(), L.ew64.get());
   CPM_CUDA_TRY(cudaGetLastError());
+  {
+    DBuf<uint32_t> erec2(np);
+    DBuf<float> efr2((size_t)L.dim * np);
+    DBuf<double> ew2((size_t)4 * L.dim * np);
+    if (ntiles > 0)
+      k_tile_sort<<<(unsigned)ntiles, 256, 0, st>>>(L.tile_start.get(), np, L.dim, L.erec.get(),
+                                                    L.efr32.get(), L.ew64.get(), erec2.get(),
+                                                    efr2.get(), ew2.get());
+    CPM_CUDA_TRY(cudaGetLastError());
+    CPM_CUDA_TRY(cudaStreamSynchronize(st));
+    L.erec = std::move(erec2);
+    L.efr32 = std::move(efr2);
+    L.ew64 = std::move(ew2);
+  }
   int32_t herr = 0;
   CPM_CUDA_TRY(cudaMemcpyAsync(&herr, err.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
   CPM_CUDA_TRY(cudaStreamSynchronize(st));

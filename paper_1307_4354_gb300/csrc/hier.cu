@@ -84,13 +84,9 @@ struct HLevel {
   DBuf<double> dM64;  // diag(M)
   Transfer R;  // restriction: targets = B of level l+1, source = this level
   Transfer P;  // prolongation: targets = B of this level, source = level l+1
-  Work<double> w64;
-  Work<float> w32;
 
   template <typename T>
   LevelView<T> view() const;
-  template <typename T>
-  Work<T>& work();
   template <typename T>
   const T* cvec() const;
   template <typename T>
@@ -145,8 +141,6 @@ LevelView<float> HLevel::view<float>() const {
   v.nbr = lev->nbr.get();
   return v;
 }
-template <> Work<double>& HLevel::work<double>() { return w64; }
-template <> Work<float>& HLevel::work<float>() { return w32; }
 template <> const double* HLevel::cvec<double>() const { return c64.get(); }
 template <> const float* HLevel::cvec<float>() const { return c32.get(); }
 template <> const double* HLevel::dA<double>() const { return dA64.get(); }
@@ -167,6 +161,39 @@ TransferView<float> tview<float>(const Transfer& t, int dim) {
 
 using namespace cpm;
 
+// Everything one solve mutates: per-level work vectors, the finest-level
+// solve vectors, norms, a stream and the captured graphs.  A hierarchy owns one
+// workspace; a batch gives every (hierarchy, right-hand side) its own.
+struct Workspace {
+  std::vector<cpm::Work<double>> w64;
+  std::vector<cpm::Work<float>> w32;
+  cpm::DBuf<double> part;   // norm partials (2 per block)
+  int part_blocks = 0;
+  cpm::DBuf<double> own_norms;  // [max, sumsq, 1/max, -] unless norms points elsewhere
+  double* norms = nullptr;
+  cpm::DBuf<double> normf;  // norms of f
+  cpm::DBuf<double> u_own, f_own, r64, d64;
+  cpm::DBuf<float> r32, d32;
+  cudaStream_t hs = nullptr;
+  cudaEvent_t ev = nullptr;
+  // graphs of one outer step: FP64, mixed, mixed with the learned smoother
+  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
+  int64_t graph_kernels[3] = {0, 0, 0};
+  int32_t graph_inner[3] = {0, 0, 0};
+  double* pinned = nullptr;
+  template <typename T>
+  cpm::Work<T>& work(int l);
+  ~Workspace() {
+    for (auto& g : graph)
+      if (g) cudaGraphExecDestroy(g);
+    if (ev) cudaEventDestroy(ev);
+    if (hs) cudaStreamDestroy(hs);
+    if (pinned) cudaFreeHost(pinned);
+  }
+};
+template <> cpm::Work<double>& Workspace::work<double>(int l) { return w64[l]; }
+template <> cpm::Work<float>& Workspace::work<float>(int l) { return w32[l]; }
+
 struct cpm_hier_s {
   cpm_surface surface;
   cpm_mg_opts opts;
@@ -177,39 +204,49 @@ struct cpm_hier_s {
   int32_t nc = 0;
   int32_t coarse_mode = 0;    // 0: FP64 inverse, 1: FP32 inverse (+FP64 refinement), 2: sweeps
   int32_t coarse_sweeps = 0;
-  DBuf<double> part;   // norm partials (2 per block)
-  int part_blocks = 0;
-  DBuf<double> norms;  // [max, sumsq, 1/max]
-  DBuf<double> normf;  // norms of f
-  DBuf<double> u_own, f_own, r64, d64;
-  DBuf<float> r32, d32;
-  cudaStream_t hs = nullptr;
-  cudaEvent_t ev = nullptr;
-  // graphs of one outer step: FP64, mixed, mixed with the learned smoother
-  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
-  int64_t graph_kernels[3] = {0, 0, 0};
-  int32_t graph_inner[3] = {0, 0, 0};
   cpm_mlp mlp = nullptr;
   std::unique_ptr<cpm::MlpLevelData> mlpd;
   bool learned_active = false;
-  double* pinned = nullptr;
-  ~cpm_hier_s() {
-    for (auto& g : graph)
-      if (g) cudaGraphExecDestroy(g);
-    if (ev) cudaEventDestroy(ev);
-    if (hs) cudaStreamDestroy(hs);
-    if (pinned) cudaFreeHost(pinned);
-  }
+  Workspace ws;
 };
+
+namespace cpm {
+// Allocate the work vectors of every level and the solve vectors.
+static void alloc_workspace(const cpm_hier_s& H, Workspace& W, double* norms_slot = nullptr) {
+  W.w64.resize(H.L.size());
+  W.w32.resize(H.L.size());
+  for (size_t l = 0; l < H.L.size(); ++l) {
+    const int64_t nB = H.L[l].lev->nB, np = H.L[l].lev->nplus();
+    W.w64[l].alloc(nB, np);
+    W.w32[l].alloc(nB, np);
+  }
+  const int64_t nB0 = H.L[0].lev->nB;
+  W.part_blocks = (int)std::max<int64_t>(nblk(nB0, 256), kNormBlocks);
+  W.part.alloc(2 * (size_t)W.part_blocks);
+  W.own_norms.alloc(4);
+  W.norms = norms_slot ? norms_slot : W.own_norms.get();
+  W.normf.alloc(4);
+  W.u_own.alloc(nB0);
+  W.f_own.alloc(nB0);
+  W.r64.alloc(nB0);
+  W.d64.alloc(nB0);
+  W.r32.alloc(nB0);
+  W.d32.alloc(nB0);
+  CPM_CUDA_TRY(cudaStreamCreateWithFlags(&W.hs, cudaStreamNonBlocking));
+  CPM_CUDA_TRY(cudaEventCreateWithFlags(&W.ev, cudaEventDisableTiming));
+  CPM_CUDA_TRY(cudaMallocHost(&W.pinned, 8 * sizeof(double)));
+}
+}  // namespace cpm
 
 namespace cpm {
 
 // ----------------------------------------------------------------- level ops
 template <typename T>
-static void smooth(cpm_hier_s* H, int l, const T* f, T* u, int sweeps, cudaStream_t st) {
+static void smooth(cpm_hier_s* H, Workspace& W, int l, const T* f, T* u, int sweeps,
+                   cudaStream_t st) {
   HLevel& lv = H->L[l];
   const LevelView<T> v = lv.view<T>();
-  Work<T>& w = lv.work<T>();
+  Work<T>& w = W.work<T>(l);
   const T omega = (T)H->opts.omega;
   const T cval = (T)H->c;
   for (int s = 0; s < sweeps; ++s) {
@@ -226,10 +263,11 @@ static void smooth(cpm_hier_s* H, int l, const T* f, T* u, int sweeps, cudaStrea
 
 // r = f - A u (Jacobi smoother) or f - (cI - L) u (Ruuth-Merriman, Algorithm 4.1 step 2).
 template <typename T>
-static void transfer_residual(cpm_hier_s* H, int l, const T* f, const T* u, T* r, cudaStream_t st) {
+static void transfer_residual(cpm_hier_s* H, Workspace& W, int l, const T* f, const T* u, T* r,
+                              cudaStream_t st) {
   HLevel& lv = H->L[l];
   const LevelView<T> v = lv.view<T>();
-  Work<T>& w = lv.work<T>();
+  Work<T>& w = W.work<T>(l);
   if (H->opts.smoother == CPM_SMOOTH_RM) {
     launch_rm_resid<T>(v, u, f, lv.cvec<T>(), (T)H->c, r, st);
   } else if (H->opts.residual_mode == 1) {
@@ -247,7 +285,7 @@ static void transfer_residual(cpm_hier_s* H, int l, const T* f, const T* u, T* r
 
 // Coarsest level: explicit FP64 inverse, or weighted Jacobi sweeps from zero.
 template <typename T>
-static void coarse_solve(cpm_hier_s* H, const T* f, T* u, cudaStream_t st) {
+static void coarse_solve(cpm_hier_s* H, Workspace& W, const T* f, T* u, cudaStream_t st) {
   const int l = (int)H->L.size() - 1;
   if (H->coarse_mode == 0) {
     launch_coarse_gemv<T>(H->Ainv.get(), f, u, H->nc, st);
@@ -260,10 +298,10 @@ static void coarse_solve(cpm_hier_s* H, const T* f, T* u, cudaStream_t st) {
       HLevel& lv = H->L[l];
       const LevelView<double> v = lv.view<double>();
       for (int it = 0; it < 2; ++it) {
-        launch_extend<double>(v, u, lv.w64.w.get(), (int32_t)v.nplus, st);
-        launch_lap<double>(v, LAP_RESID, u, lv.w64.w.get(), f, lv.c64.get(), H->c, nullptr, 0.0,
-                           lv.w64.r.get(), nullptr, nullptr, 0, st);
-        launch_coarse_gemv32<double>(H->Ainv32.get(), lv.w64.r.get(), u, H->nc, true, st);
+        launch_extend<double>(v, u, W.w64[l].w.get(), (int32_t)v.nplus, st);
+        launch_lap<double>(v, LAP_RESID, u, W.w64[l].w.get(), f, lv.c64.get(), H->c, nullptr, 0.0,
+                           W.w64[l].r.get(), nullptr, nullptr, 0, st);
+        launch_coarse_gemv32<double>(H->Ainv32.get(), W.w64[l].r.get(), u, H->nc, true, st);
       }
     }
     return;
@@ -271,7 +309,7 @@ static void coarse_solve(cpm_hier_s* H, const T* f, T* u, cudaStream_t st) {
   CPM_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(T) * H->L[l].lev->nB, st));
   HLevel& lv = H->L[l];
   const LevelView<T> v = lv.view<T>();
-  Work<T>& w = lv.work<T>();
+  Work<T>& w = W.work<T>(l);
   for (int s = 0; s < H->coarse_sweeps; ++s) {
     launch_extend<T>(v, u, w.w.get(), (int32_t)v.nplus, st);
     launch_lap<T>(v, LAP_JACOBI, u, w.w.get(), f, lv.cvec<T>(), (T)H->c, lv.dA<T>(),
@@ -280,16 +318,16 @@ static void coarse_solve(cpm_hier_s* H, const T* f, T* u, cudaStream_t st) {
 }
 
 template <typename T>
-static void vcycle_level(cpm_hier_s* H, int l, const T* f, T* u, cudaStream_t st) {
+static void vcycle_level(cpm_hier_s* H, Workspace& W, int l, const T* f, T* u, cudaStream_t st) {
   const int nl = (int)H->L.size();
   if (l == nl - 1) {
-    coarse_solve<T>(H, f, u, st);
+    coarse_solve<T>(H, W, f, u, st);
     return;
   }
   HLevel& lv = H->L[l];
   HLevel& cv = H->L[l + 1];
-  Work<T>& w = lv.work<T>();
-  Work<T>& cw = cv.work<T>();
+  Work<T>& w = W.work<T>(l);
+  Work<T>& cw = W.work<T>(l + 1);
   int pre = H->opts.nu1;
   if constexpr (sizeof(T) == 4) {
     if (l == 0 && H->learned_active && pre > 0) {
@@ -302,40 +340,41 @@ static void vcycle_level(cpm_hier_s* H, int l, const T* f, T* u, cudaStream_t st
       --pre;
     }
   }
-  smooth<T>(H, l, f, u, pre, st);
-  transfer_residual<T>(H, l, f, u, w.r.get(), st);
+  smooth<T>(H, W, l, f, u, pre, st);
+  transfer_residual<T>(H, W, l, f, u, w.r.get(), st);
   launch_transfer<T>(tview<T>(lv.R, lv.lev->dim), w.r.get(), cw.f.get(), false, st);
   if (l + 1 < nl - 1)
     CPM_CUDA_TRY(cudaMemsetAsync(cw.u.get(), 0, sizeof(T) * cv.lev->nB, st));
-  vcycle_level<T>(H, l + 1, cw.f.get(), cw.u.get(), st);
+  vcycle_level<T>(H, W, l + 1, cw.f.get(), cw.u.get(), st);
   launch_transfer<T>(tview<T>(lv.P, lv.lev->dim), cw.u.get(), u, true, st);
-  smooth<T>(H, l, f, u, H->opts.nu2, st);
+  smooth<T>(H, W, l, f, u, H->opts.nu2, st);
 }
 
 // FP64 outer residual r = f - A u on the finest level with norms into H->norms.
-static void outer_residual(cpm_hier_s* H, const double* f, const double* u, double* r, cudaStream_t st) {
+static void outer_residual(cpm_hier_s* H, Workspace& W, const double* f, const double* u, double* r,
+                           cudaStream_t st) {
   HLevel& lv = H->L[0];
   const LevelView<double> v = lv.view<double>();
-  launch_extend<double>(v, u, lv.w64.w.get(), (int32_t)v.nplus, st);
-  launch_lap<double>(v, LAP_RESID, u, lv.w64.w.get(), f, lv.c64.get(), H->c, nullptr, 0.0, r, nullptr,
-                     H->part.get(), H->part_blocks, st);
-  launch_norm_final(H->part.get(), nblk(v.nB, 256), H->norms.get(), st);
+  launch_extend<double>(v, u, W.w64[0].w.get(), (int32_t)v.nplus, st);
+  launch_lap<double>(v, LAP_RESID, u, W.w64[0].w.get(), f, lv.c64.get(), H->c, nullptr, 0.0, r, nullptr,
+                     W.part.get(), W.part_blocks, st);
+  launch_norm_final(W.part.get(), nblk(v.nB, 256), W.norms, st);
 }
 
 // One outer iteration after the residual: u += V(0, r), then the new residual.
-static void outer_step(cpm_hier_s* H, int mode, int inner, cudaStream_t st) {
+static void outer_step(cpm_hier_s* H, Workspace& W, int mode, int inner, cudaStream_t st) {
   const int64_t nB = H->L[0].lev->nB;
   if (mode == CPM_SOLVE_F64) {
-    CPM_CUDA_TRY(cudaMemsetAsync(H->d64.get(), 0, sizeof(double) * nB, st));
-    vcycle_level<double>(H, 0, H->r64.get(), H->d64.get(), st);
-    launch_axpy64(H->u_own.get(), H->d64.get(), nB, st);
+    CPM_CUDA_TRY(cudaMemsetAsync(W.d64.get(), 0, sizeof(double) * nB, st));
+    vcycle_level<double>(H, W, 0, W.r64.get(), W.d64.get(), st);
+    launch_axpy64(W.u_own.get(), W.d64.get(), nB, st);
   } else {
-    launch_scale_to_f32(H->r64.get(), H->norms.get(), H->r32.get(), nB, st);
-    CPM_CUDA_TRY(cudaMemsetAsync(H->d32.get(), 0, sizeof(float) * nB, st));
-    for (int j = 0; j < inner; ++j) vcycle_level<float>(H, 0, H->r32.get(), H->d32.get(), st);
-    launch_axpy_scaled(H->u_own.get(), H->d32.get(), H->norms.get(), nB, st);
+    launch_scale_to_f32(W.r64.get(), W.norms, W.r32.get(), nB, st);
+    CPM_CUDA_TRY(cudaMemsetAsync(W.d32.get(), 0, sizeof(float) * nB, st));
+    for (int j = 0; j < inner; ++j) vcycle_level<float>(H, W, 0, W.r32.get(), W.d32.get(), st);
+    launch_axpy_scaled(W.u_own.get(), W.d32.get(), W.norms, nB, st);
   }
-  outer_residual(H, H->f_own.get(), H->u_own.get(), H->r64.get(), st);
+  outer_residual(H, W, W.f_own.get(), W.u_own.get(), W.r64.get(), st);
 }
 
 }  // namespace cpm
@@ -587,8 +626,6 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
     CPM_CUDA_TRY(cudaGetLastError());
     CPM_CUDA_TRY(cudaStreamSynchronize(st));
     lv.dM64 = std::move(dM);
-    lv.w64.alloc(nB, np);
-    lv.w32.alloc(nB, np);
   }
   init_coarse_gemv();
   // coarsest: dense A = diag(c) - M, inverted in place (FP64)
@@ -618,20 +655,7 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
   CPM_CHECK(!(herr & 1), CPM_ERR_SINGULAR, "coarsest-level matrix is singular");
 
   // solve buffers
-  const int64_t nB0 = f0.nB;
-  H->part_blocks = (int)std::max<int64_t>(nblk(nB0, 256), kNormBlocks);
-  H->part.alloc(2 * (size_t)H->part_blocks);
-  H->norms.alloc(4);
-  H->normf.alloc(4);
-  H->u_own.alloc(nB0);
-  H->f_own.alloc(nB0);
-  H->r64.alloc(nB0);
-  H->d64.alloc(nB0);
-  H->r32.alloc(nB0);
-  H->d32.alloc(nB0);
-  CPM_CUDA_TRY(cudaStreamCreateWithFlags(&H->hs, cudaStreamNonBlocking));
-  CPM_CUDA_TRY(cudaEventCreateWithFlags(&H->ev, cudaEventDisableTiming));
-  CPM_CUDA_TRY(cudaMallocHost(&H->pinned, 8 * sizeof(double)));
+  alloc_workspace(*H, H->ws);
   *out = H.release();
   CPM_API_END
 }
@@ -656,14 +680,14 @@ cpm_status cpm_apply(cpm_hier h, int32_t level, int32_t prec, const void* u, voi
   HLevel& lv = h->L[level];
   if (prec == CPM_F64) {
     const auto v = lv.view<double>();
-    launch_extend<double>(v, (const double*)u, lv.w64.w.get(), (int32_t)v.nplus, st);
-    launch_lap<double>(v, LAP_APPLY, (const double*)u, lv.w64.w.get(), nullptr, nullptr, 0.0, nullptr,
+    launch_extend<double>(v, (const double*)u, h->ws.w64[level].w.get(), (int32_t)v.nplus, st);
+    launch_lap<double>(v, LAP_APPLY, (const double*)u, h->ws.w64[level].w.get(), nullptr, nullptr, 0.0, nullptr,
                        0.0, (double*)Mu, nullptr, nullptr, 0, st);
   } else {
     CPM_CHECK(prec == CPM_F32, CPM_ERR_ARG, "unknown precision");
     const auto v = lv.view<float>();
-    launch_extend<float>(v, (const float*)u, lv.w32.w.get(), (int32_t)v.nplus, st);
-    launch_lap<float>(v, LAP_APPLY, (const float*)u, lv.w32.w.get(), nullptr, nullptr, 0.f, nullptr,
+    launch_extend<float>(v, (const float*)u, h->ws.w32[level].w.get(), (int32_t)v.nplus, st);
+    launch_lap<float>(v, LAP_APPLY, (const float*)u, h->ws.w32[level].w.get(), nullptr, nullptr, 0.f, nullptr,
                       0.f, (float*)Mu, nullptr, nullptr, 0, st);
   }
   CPM_CUDA_TRY(cudaGetLastError());
@@ -698,10 +722,10 @@ cpm_status cpm_smooth(cpm_hier h, int32_t level, int32_t prec, const void* f, vo
   CPM_CHECK(sweeps >= 0, CPM_ERR_ARG, "sweeps must be >= 0");
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == CPM_F64)
-    smooth<double>(h, level, (const double*)f, (double*)u, sweeps, st);
+    smooth<double>(h, h->ws, level, (const double*)f, (double*)u, sweeps, st);
   else {
     CPM_CHECK(prec == CPM_F32, CPM_ERR_ARG, "unknown precision");
-    smooth<float>(h, level, (const float*)f, (float*)u, sweeps, st);
+    smooth<float>(h, h->ws, level, (const float*)f, (float*)u, sweeps, st);
   }
   CPM_CUDA_TRY(cudaGetLastError());
   CPM_API_END
@@ -712,10 +736,10 @@ cpm_status cpm_vcycle(cpm_hier h, int32_t prec, const void* f, void* u, cpm_stre
   CPM_CHECK(h != nullptr && u != nullptr && f != nullptr, CPM_ERR_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
   if (prec == CPM_F64)
-    vcycle_level<double>(h, 0, (const double*)f, (double*)u, st);
+    vcycle_level<double>(h, h->ws, 0, (const double*)f, (double*)u, st);
   else {
     CPM_CHECK(prec == CPM_F32, CPM_ERR_ARG, "unknown precision");
-    vcycle_level<float>(h, 0, (const float*)f, (float*)u, st);
+    vcycle_level<float>(h, h->ws, 0, (const float*)f, (float*)u, st);
   }
   CPM_CUDA_TRY(cudaGetLastError());
   CPM_API_END
@@ -724,7 +748,7 @@ cpm_status cpm_vcycle(cpm_hier h, int32_t prec, const void* f, void* u, cpm_stre
 cpm_status cpm_residual(cpm_hier h, const double* f, const double* u, double* r, cpm_stream stream) {
   CPM_API_BEGIN
   CPM_CHECK(h != nullptr && u != nullptr && f != nullptr && r != nullptr, CPM_ERR_ARG, "NULL argument");
-  outer_residual(h, f, u, r, (cudaStream_t)stream);
+  outer_residual(h, h->ws, f, u, r, (cudaStream_t)stream);
   CPM_CUDA_TRY(cudaGetLastError());
   CPM_API_END
 }
@@ -735,12 +759,13 @@ cpm_status cpm_residual_norms(cpm_hier h, const double* f, const double* u, doub
   CPM_CHECK(h != nullptr && u != nullptr && f != nullptr, CPM_ERR_ARG, "NULL argument");
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t nB = h->L[0].lev->nB;
-  launch_norm_partials<double>(f, nB, h->part.get(), st);
-  launch_norm_final(h->part.get(), kNormBlocks, h->normf.get(), st);
-  outer_residual(h, f, u, h->r64.get(), st);
+  Workspace& W = h->ws;
+  launch_norm_partials<double>(f, nB, W.part.get(), st);
+  launch_norm_final(W.part.get(), kNormBlocks, W.normf.get(), st);
+  outer_residual(h, W, f, u, W.r64.get(), st);
   double hn[3], hf[3];
-  CPM_CUDA_TRY(cudaMemcpyAsync(hn, h->norms.get(), 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
-  CPM_CUDA_TRY(cudaMemcpyAsync(hf, h->normf.get(), 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaMemcpyAsync(hn, W.norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaMemcpyAsync(hf, W.normf.get(), 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
   if (rel_inf) *rel_inf = hf[0] > 0 ? hn[0] / hf[0] : hn[0];
   if (abs_l2) *abs_l2 = std::sqrt(hn[1]);
@@ -757,10 +782,8 @@ cpm_status cpm_residual_norms_noalloc(cpm_hier h, const double* f, const double*
   CPM_API_END
 }
 
-cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opts* opts_in,
-                     cpm_solve_report* report, cpm_stream stream) {
-  CPM_API_BEGIN
-  CPM_CHECK(h != nullptr && u != nullptr && f != nullptr, CPM_ERR_ARG, "NULL argument");
+// Options with defaults filled in and checked.
+static cpm_solve_opts solve_opts(const cpm_solve_opts* opts_in) {
   cpm_solve_opts o{};
   o.use_graph = 1;
   if (opts_in) o = *opts_in;
@@ -769,69 +792,77 @@ cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opt
   CPM_CHECK(o.inner_cycles <= 16, CPM_ERR_ARG, "inner_cycles must be <= 16");
   if (o.max_iter <= 0) o.max_iter = 100;
   CPM_CHECK(o.mode == CPM_SOLVE_F64 || o.mode == CPM_SOLVE_MIXED, CPM_ERR_ARG, "unknown mode");
+  return o;
+}
+
+// Graph of one outer step of workspace W (captured on first use).
+static void capture_outer_step(cpm_hier_s* h, Workspace& W, int idx, int mode, int inner,
+                               cudaStream_t st) {
+  cudaGraphExec_t& gx = W.graph[idx];
+  if (gx && W.graph_inner[idx] != inner) {
+    cudaGraphExecDestroy(gx);
+    gx = nullptr;
+  }
+  if (gx) return;
+  W.graph_inner[idx] = inner;
+  cudaGraph_t g;
+  CPM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  set_capturing(true);
+  try {
+    outer_step(h, W, mode, inner, st);
+  } catch (...) {
+    set_capturing(false);
+    cudaStreamEndCapture(st, &g);
+    throw;
+  }
+  set_capturing(false);
+  CPM_CUDA_TRY(cudaStreamEndCapture(st, &g));
+  size_t nn = 0;
+  CPM_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CPM_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &nn));
+  int64_t nk = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    CPM_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+    nk += t == cudaGraphNodeTypeKernel;
+  }
+  W.graph_kernels[idx] = nk;
+  CPM_CUDA_TRY(cudaGraphInstantiate(&gx, g, 0));
+  CPM_CUDA_TRY(cudaGraphDestroy(g));
+}
+
+// One complete solve with workspace W (synchronous); returns the status.
+static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
+                           const cpm_solve_opts* opts_in, cpm_solve_report* report, cpm_stream stream) {
+  CPM_CHECK(h != nullptr && u != nullptr && f != nullptr, CPM_ERR_ARG, "NULL argument");
+  const cpm_solve_opts o = solve_opts(opts_in);
   const auto t0 = std::chrono::steady_clock::now();
   cudaStream_t us = (cudaStream_t)stream;
-  cudaStream_t st = h->hs;
+  cudaStream_t st = W.hs;
   const int64_t nB = h->L[0].lev->nB;
-  CPM_CUDA_TRY(cudaEventRecord(h->ev, us));
-  CPM_CUDA_TRY(cudaStreamWaitEvent(st, h->ev, 0));
-  CPM_CUDA_TRY(cudaMemcpyAsync(h->f_own.get(), f, nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CPM_CUDA_TRY(cudaEventRecord(W.ev, us));
+  CPM_CUDA_TRY(cudaStreamWaitEvent(st, W.ev, 0));
+  CPM_CUDA_TRY(cudaMemcpyAsync(W.f_own.get(), f, nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
   if (o.zero_init)
-    CPM_CUDA_TRY(cudaMemsetAsync(h->u_own.get(), 0, nB * sizeof(double), st));
+    CPM_CUDA_TRY(cudaMemsetAsync(W.u_own.get(), 0, nB * sizeof(double), st));
   else
-    CPM_CUDA_TRY(cudaMemcpyAsync(h->u_own.get(), u, nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  launch_norm_partials<double>(h->f_own.get(), nB, h->part.get(), st);
-  launch_norm_final(h->part.get(), kNormBlocks, h->normf.get(), st);
-  CPM_CUDA_TRY(cudaMemcpyAsync(h->pinned + 4, h->normf.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
-  outer_residual(h, h->f_own.get(), h->u_own.get(), h->r64.get(), st);
-  CPM_CUDA_TRY(cudaMemcpyAsync(h->pinned, h->norms.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
+    CPM_CUDA_TRY(cudaMemcpyAsync(W.u_own.get(), u, nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  launch_norm_partials<double>(W.f_own.get(), nB, W.part.get(), st);
+  launch_norm_final(W.part.get(), kNormBlocks, W.normf.get(), st);
+  CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned + 4, W.normf.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
+  outer_residual(h, W, W.f_own.get(), W.u_own.get(), W.r64.get(), st);
+  CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.norms, sizeof(double), cudaMemcpyDeviceToHost, st));
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
-  const double fmax = h->pinned[4];
+  const double fmax = W.pinned[4];
   CPM_CHECK(std::isfinite(fmax), CPM_ERR_ARG, "f is not finite");
   const double fn = fmax > 0 ? fmax : 1.0;
   CPM_CHECK(!o.learned || (o.mode == CPM_SOLVE_MIXED && h->mlp), CPM_ERR_ARG,
             "learned smoothing needs mode MIXED and cpm_hier_set_smoother");
   h->learned_active = false;
   int gi = o.mode;
-  auto graph_for = [&](int idx) -> cudaGraphExec_t& {
-    cudaGraphExec_t& g = h->graph[idx];
-    if (g && h->graph_inner[idx] != o.inner_cycles) {
-      cudaGraphExecDestroy(g);
-      g = nullptr;
-    }
-    return g;
-  };
-  auto capture = [&](int idx) {
-    cudaGraphExec_t& gx = h->graph[idx];
-    h->graph_inner[idx] = o.inner_cycles;
-    cudaGraph_t g;
-    CPM_CUDA_TRY(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-    set_capturing(true);
-    try {
-      outer_step(h, o.mode, o.inner_cycles, st);
-    } catch (...) {
-      set_capturing(false);
-      cudaStreamEndCapture(st, &g);
-      throw;
-    }
-    set_capturing(false);
-    CPM_CUDA_TRY(cudaStreamEndCapture(st, &g));
-    size_t nn = 0;
-    CPM_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &nn));
-    std::vector<cudaGraphNode_t> nodes(nn);
-    CPM_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &nn));
-    int64_t nk = 0;
-    for (auto nd : nodes) {
-      cudaGraphNodeType t;
-      CPM_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
-      nk += t == cudaGraphNodeTypeKernel;
-    }
-    h->graph_kernels[idx] = nk;
-    CPM_CUDA_TRY(cudaGraphInstantiate(&gx, g, 0));
-    CPM_CUDA_TRY(cudaGraphDestroy(g));
-  };
   cpm_solve_report rep{};
-  double rel = h->pinned[0] / fn, best = rel;
+  double rel = W.pinned[0] / fn, best = rel;
   cpm_status result = CPM_ERR_NOT_CONVERGED;
   int it = 0;
   // learned smoothing: iteration 0 runs plain Jacobi V-cycles and sets the
@@ -850,17 +881,16 @@ cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opt
     h->learned_active = learned_on;
     gi = learned_on ? 2 : o.mode;
     if (o.use_graph) {
-      cudaGraphExec_t& g = graph_for(gi);
-      if (!g) capture(gi);
-      CPM_CUDA_TRY(cudaGraphLaunch(h->graph[gi], st));
-      count_launch(h->graph_kernels[gi]);
+      capture_outer_step(h, W, gi, o.mode, o.inner_cycles, st);
+      CPM_CUDA_TRY(cudaGraphLaunch(W.graph[gi], st));
+      count_launch(W.graph_kernels[gi]);
     } else {
-      outer_step(h, o.mode, o.inner_cycles, st);
+      outer_step(h, W, o.mode, o.inner_cycles, st);
     }
-    CPM_CUDA_TRY(cudaMemcpyAsync(h->pinned, h->norms.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
+    CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.norms, sizeof(double), cudaMemcpyDeviceToHost, st));
     CPM_CUDA_TRY(cudaStreamSynchronize(st));
     const double prev = rel;
-    rel = h->pinned[0] / fn;
+    rel = W.pinned[0] / fn;
     if (o.learned) {
       const double fac = prev > 0 ? rel / prev : 0.0;
       if (it == 0) {
@@ -879,19 +909,25 @@ cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opt
   h->learned_active = false;
   rep.jacobi_factor = ref_factor;
   rep.learned_factor = rep.learned_iters ? std::exp(learned_log / rep.learned_iters) : 0.0;
-  CPM_CUDA_TRY(cudaMemcpyAsync(u, h->u_own.get(), nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
-  CPM_CUDA_TRY(cudaEventRecord(h->ev, st));
-  CPM_CUDA_TRY(cudaStreamWaitEvent(us, h->ev, 0));
+  CPM_CUDA_TRY(cudaMemcpyAsync(u, W.u_own.get(), nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  CPM_CUDA_TRY(cudaEventRecord(W.ev, st));
+  CPM_CUDA_TRY(cudaStreamWaitEvent(us, W.ev, 0));
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
   rep.iters = it;
   rep.converged = result == CPM_OK;
   rep.rel_residual = rel;
   rep.seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
   if (report) *report = rep;
-  if (result != CPM_OK) {
+  if (result != CPM_OK)
     cpm::set_last_error(result == CPM_ERR_DIVERGED ? "residual diverged" : "max_iter reached");
-    return result;
-  }
+  return result;
+}
+
+cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opts* opts_in,
+                     cpm_solve_report* report, cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr, CPM_ERR_ARG, "NULL argument");
+  return solve_ws(h, h->ws, f, u, opts_in, report, stream);
   CPM_API_END
 }
 
@@ -956,16 +992,16 @@ cpm_status cpm_mlp_destroy(cpm_mlp m) {
 cpm_status cpm_hier_set_smoother(cpm_hier h, cpm_mlp m) {
   CPM_API_BEGIN
   CPM_CHECK(h != nullptr, CPM_ERR_ARG, "hierarchy is NULL");
-  if (h->graph[2]) {
-    cudaGraphExecDestroy(h->graph[2]);
-    h->graph[2] = nullptr;
+  if (h->ws.graph[2]) {
+    cudaGraphExecDestroy(h->ws.graph[2]);
+    h->ws.graph[2] = nullptr;
   }
   h->mlp = m;
   if (m && !h->mlpd) {
     CPM_CHECK(h->L[0].lev->dim == 3, CPM_ERR_ARG, "the learned smoother is for surfaces in 3-D");
     h->mlpd.reset(new MlpLevelData);
-    h->mlpd->build(*h->L[0].lev, h->L[0].dM64.get(), h->hs);
-    CPM_CUDA_TRY(cudaStreamSynchronize(h->hs));
+    h->mlpd->build(*h->L[0].lev, h->L[0].dM64.get(), h->ws.hs);
+    CPM_CUDA_TRY(cudaStreamSynchronize(h->ws.hs));
   }
   CPM_API_END
 }
@@ -1024,6 +1060,313 @@ cpm_status cpm_mlp_train_step(cpm_hier h, const float* r, float lr, double* loss
 cpm_status cpm_hier_destroy(cpm_hier h) {
   CPM_API_BEGIN
   delete h;
+  CPM_API_END
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------- batches
+struct cpm_batch_s {
+  std::vector<cpm_hier> H;       // per system
+  std::vector<std::unique_ptr<Workspace>> W;
+  int32_t n_rhs = 1;
+  std::string cache;
+  cpm::DBuf<double> norms_all;   // 4 per system
+  double* host_norms = nullptr;  // pinned, 4 per system
+  cudaStream_t ms = nullptr;
+  std::vector<cudaStream_t> fs;  // branch streams
+  cudaEvent_t ev_fork = nullptr, t0 = nullptr, t1 = nullptr;
+  std::vector<cudaEvent_t> ev_join;
+  cudaGraphExec_t graph = nullptr;
+  int graph_k = 0, graph_mode = -1, graph_inner = -1;
+  std::vector<int> graph_sys;    // systems in the current graph
+  int64_t graph_kernels = 0;
+  int32_t chosen = 0;
+  double tune_ms[8] = {0};
+  ~cpm_batch_s() {
+    if (graph) cudaGraphExecDestroy(graph);
+    for (auto e : ev_join) cudaEventDestroy(e);
+    if (ev_fork) cudaEventDestroy(ev_fork);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    for (auto s : fs) cudaStreamDestroy(s);
+    if (ms) cudaStreamDestroy(ms);
+    if (host_norms) cudaFreeHost(host_norms);
+  }
+};
+
+namespace cpm {
+
+static constexpr int kMaxBranches = 32;
+
+// Tune-cache key: the batch shape (number of systems and the finest band
+// sizes), so a cached concurrency is reused only for the same workload.
+static std::string batch_key(const cpm_batch_s& b) {
+  uint64_t h = 1469598103934665603ull;
+  for (auto* hh : b.H) {
+    h ^= (uint64_t)hh->L[0].lev->nB;
+    h *= 1099511628211ull;
+  }
+  return "n" + std::to_string(b.H.size()) + "_" + std::to_string(h);
+}
+
+static int cache_lookup(const cpm_batch_s& b) {
+  if (b.cache.empty()) return 0;
+  FILE* fp = std::fopen(b.cache.c_str(), "r");
+  if (!fp) return 0;
+  char key[256];
+  int k = 0, found = 0;
+  const std::string want = batch_key(b);
+  while (std::fscanf(fp, "%255s %d", key, &k) == 2)
+    if (want == key && k >= 1 && k <= kMaxBranches) found = k;
+  std::fclose(fp);
+  return found;
+}
+
+static void cache_store(const cpm_batch_s& b, int k) {
+  if (b.cache.empty()) return;
+  FILE* fp = std::fopen(b.cache.c_str(), "a");
+  if (!fp) return;
+  std::fprintf(fp, "%s %d\n", batch_key(b).c_str(), k);
+  std::fclose(fp);
+}
+
+// Graph of one outer iteration of the systems in sys: K concurrent branches,
+// system sys[j] on branch j mod K.  Largest systems first so that the
+// branches finish close together.
+static void capture_batch(cpm_batch_s& b, const std::vector<int>& sys, int K, int mode, int inner) {
+  if (b.graph && b.graph_k == K && b.graph_mode == mode && b.graph_inner == inner && b.graph_sys == sys)
+    return;
+  if (b.graph) {
+    cudaGraphExecDestroy(b.graph);
+    b.graph = nullptr;
+  }
+  std::vector<int> order(sys);
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b.H[x]->L[0].lev->nB > b.H[y]->L[0].lev->nB; });
+  cudaGraph_t g;
+  CPM_CUDA_TRY(cudaStreamBeginCapture(b.ms, cudaStreamCaptureModeThreadLocal));
+  set_capturing(true);
+  try {
+    CPM_CUDA_TRY(cudaEventRecord(b.ev_fork, b.ms));
+    for (int k = 0; k < K; ++k) CPM_CUDA_TRY(cudaStreamWaitEvent(b.fs[k], b.ev_fork, 0));
+    for (size_t j = 0; j < order.size(); ++j)
+      outer_step(b.H[order[j]], *b.W[order[j]], mode, inner, b.fs[j % K]);
+    for (int k = 0; k < K; ++k) {
+      CPM_CUDA_TRY(cudaEventRecord(b.ev_join[k], b.fs[k]));
+      CPM_CUDA_TRY(cudaStreamWaitEvent(b.ms, b.ev_join[k], 0));
+    }
+  } catch (...) {
+    set_capturing(false);
+    cudaStreamEndCapture(b.ms, &g);
+    throw;
+  }
+  set_capturing(false);
+  CPM_CUDA_TRY(cudaStreamEndCapture(b.ms, &g));
+  size_t nn = 0;
+  CPM_CUDA_TRY(cudaGraphGetNodes(g, nullptr, &nn));
+  std::vector<cudaGraphNode_t> nodes(nn);
+  CPM_CUDA_TRY(cudaGraphGetNodes(g, nodes.data(), &nn));
+  int64_t nk = 0;
+  for (auto nd : nodes) {
+    cudaGraphNodeType t;
+    CPM_CUDA_TRY(cudaGraphNodeGetType(nd, &t));
+    nk += t == cudaGraphNodeTypeKernel;
+  }
+  b.graph_kernels = nk;
+  CPM_CUDA_TRY(cudaGraphInstantiate(&b.graph, g, 0));
+  CPM_CUDA_TRY(cudaGraphDestroy(g));
+  b.graph_k = K;
+  b.graph_mode = mode;
+  b.graph_inner = inner;
+  b.graph_sys = sys;
+}
+
+}  // namespace cpm
+
+extern "C" {
+
+cpm_status cpm_build_batch(const cpm_hier* hiers, int32_t n_hier, int32_t n_rhs,
+                           const char* tune_cache, cpm_batch* out) {
+  CPM_API_BEGIN
+  CPM_CHECK(hiers != nullptr && out != nullptr && n_hier > 0 && n_rhs > 0 &&
+                (int64_t)n_hier * n_rhs <= CPM_BATCH_MAX_SYSTEMS,
+            CPM_ERR_ARG, "bad batch arguments");
+  *out = nullptr;
+  std::unique_ptr<cpm_batch_s> b(new cpm_batch_s);
+  b->n_rhs = n_rhs;
+  if (tune_cache) b->cache = tune_cache;
+  const int ns = n_hier * n_rhs;
+  b->norms_all.alloc(4 * (size_t)ns);
+  CPM_CUDA_TRY(cudaMallocHost(&b->host_norms, 4 * sizeof(double) * ns));
+  for (int i = 0; i < n_hier; ++i) {
+    CPM_CHECK(hiers[i] != nullptr, CPM_ERR_ARG, "NULL hierarchy");
+    for (int k = 0; k < n_rhs; ++k) {
+      const int s = i * n_rhs + k;
+      b->H.push_back(hiers[i]);
+      b->W.emplace_back(new Workspace);
+      alloc_workspace(*hiers[i], *b->W.back(), b->norms_all.get() + 4 * (size_t)s);
+    }
+  }
+  CPM_CUDA_TRY(cudaStreamCreateWithFlags(&b->ms, cudaStreamNonBlocking));
+  b->fs.resize(kMaxBranches);
+  b->ev_join.resize(kMaxBranches);
+  for (int k = 0; k < kMaxBranches; ++k) {
+    CPM_CUDA_TRY(cudaStreamCreateWithFlags(&b->fs[k], cudaStreamNonBlocking));
+    CPM_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming));
+  }
+  CPM_CUDA_TRY(cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming));
+  CPM_CUDA_TRY(cudaEventCreate(&b->t0));
+  CPM_CUDA_TRY(cudaEventCreate(&b->t1));
+  *out = b.release();
+  CPM_API_END
+}
+
+cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u,
+                           const cpm_solve_opts* opts_in, cpm_solve_report* reports,
+                           cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(b != nullptr && f != nullptr && u != nullptr, CPM_ERR_ARG, "NULL argument");
+  const cpm_solve_opts o = solve_opts(opts_in);
+  CPM_CHECK(!o.learned, CPM_ERR_ARG, "learned smoothing is not available in batches");
+  const int ns = (int)b->H.size();
+  for (int s = 0; s < ns; ++s)
+    CPM_CHECK(f[s] != nullptr && u[s] != nullptr, CPM_ERR_ARG, "NULL vector in batch");
+  const auto tstart = std::chrono::steady_clock::now();
+  cudaStream_t us = (cudaStream_t)stream;
+  CPM_CUDA_TRY(cudaEventRecord(b->ev_fork, us));
+  CPM_CUDA_TRY(cudaStreamWaitEvent(b->ms, b->ev_fork, 0));
+  for (int k = 0; k < kMaxBranches; ++k) CPM_CUDA_TRY(cudaStreamWaitEvent(b->fs[k], b->ev_fork, 0));
+  // copies in, norms of f and the initial residuals, spread over the branch streams
+  DBuf<double> fn_all(4 * (size_t)ns);
+  for (int s = 0; s < ns; ++s) {
+    Workspace& W = *b->W[s];
+    cudaStream_t st = b->fs[s % kMaxBranches];
+    const int64_t nB = b->H[s]->L[0].lev->nB;
+    CPM_CUDA_TRY(cudaMemcpyAsync(W.f_own.get(), f[s], nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (o.zero_init)
+      CPM_CUDA_TRY(cudaMemsetAsync(W.u_own.get(), 0, nB * sizeof(double), st));
+    else
+      CPM_CUDA_TRY(cudaMemcpyAsync(W.u_own.get(), u[s], nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_norm_partials<double>(W.f_own.get(), nB, W.part.get(), st);
+    launch_norm_final(W.part.get(), kNormBlocks, fn_all.get() + 4 * (size_t)s, st);
+    outer_residual(b->H[s], W, W.f_own.get(), W.u_own.get(), W.r64.get(), st);
+  }
+  for (int k = 0; k < kMaxBranches; ++k) {
+    CPM_CUDA_TRY(cudaEventRecord(b->ev_join[k], b->fs[k]));
+    CPM_CUDA_TRY(cudaStreamWaitEvent(b->ms, b->ev_join[k], 0));
+  }
+  std::vector<double> hf(4 * (size_t)ns);
+  CPM_CUDA_TRY(cudaMemcpyAsync(hf.data(), fn_all.get(), hf.size() * sizeof(double), cudaMemcpyDeviceToHost,
+                               b->ms));
+  CPM_CUDA_TRY(cudaMemcpyAsync(b->host_norms, b->norms_all.get(), 4 * sizeof(double) * ns,
+                               cudaMemcpyDeviceToHost, b->ms));
+  CPM_CUDA_TRY(cudaStreamSynchronize(b->ms));
+  std::vector<cpm_solve_report> rep(ns);
+  std::vector<double> fmax(ns), rel(ns), best(ns);
+  std::vector<int> done(ns, 0);
+  for (int s = 0; s < ns; ++s) {
+    CPM_CHECK(std::isfinite(hf[4 * (size_t)s]), CPM_ERR_ARG, "f is not finite");
+    fmax[s] = hf[4 * (size_t)s] > 0 ? hf[4 * (size_t)s] : 1.0;
+    rel[s] = best[s] = b->host_norms[4 * (size_t)s] / fmax[s];
+  }
+  // autotuner: the first outer iterations try K = 1, 2, 4, ... concurrent
+  // branches (each a real iteration of every active system)
+  std::vector<int> cand;
+  if (b->chosen == 0) b->chosen = cache_lookup(*b);
+  if (b->chosen == 0)
+    for (int k = 1; k <= std::min(ns, kMaxBranches); k *= 2) cand.push_back(k);
+  size_t ci = 0;
+  double best_ms = 1e300;
+  int best_k = b->chosen;
+  cpm_status result = CPM_OK;
+  std::vector<int> active, in_graph;
+  int it = 0;
+  for (;; ++it) {
+    bool diverged = false;
+    active.clear();
+    for (int s = 0; s < ns; ++s) {
+      if (done[s]) continue;
+      if (it < CPM_MAX_HISTORY) rep[s].history[it] = rel[s];
+      rep[s].iters = it;
+      rep[s].rel_residual = rel[s];
+      if (rel[s] <= o.tol) {
+        // the converged iterate is the result, whatever later iterations of
+        // the other systems do to this workspace
+        done[s] = 1;
+        rep[s].converged = 1;
+        CPM_CUDA_TRY(cudaMemcpyAsync(u[s], b->W[s]->u_own.get(), b->H[s]->L[0].lev->nB * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, b->ms));
+        continue;
+      }
+      if (!std::isfinite(rel[s]) || rel[s] > 1e3 * best[s]) diverged = true;
+      best[s] = std::min(best[s], rel[s]);
+      active.push_back(s);
+    }
+    if (active.empty()) break;
+    if (diverged) { result = CPM_ERR_DIVERGED; break; }
+    if (it >= o.max_iter) { result = CPM_ERR_NOT_CONVERGED; break; }
+    // the graph covers a superset of the active systems; it is re-captured
+    // over the active ones once they are at most half of it
+    if (in_graph.empty() || 2 * active.size() <= in_graph.size()) in_graph = active;
+    const int K = ci < cand.size() ? cand[ci] : (best_k > 0 ? best_k : 1);
+    capture_batch(*b, in_graph, std::min<int>(K, (int)in_graph.size()), o.mode, o.inner_cycles);
+    CPM_CUDA_TRY(cudaEventRecord(b->t0, b->ms));
+    CPM_CUDA_TRY(cudaGraphLaunch(b->graph, b->ms));
+    CPM_CUDA_TRY(cudaEventRecord(b->t1, b->ms));
+    count_launch(b->graph_kernels);
+    CPM_CUDA_TRY(cudaMemcpyAsync(b->host_norms, b->norms_all.get(), 4 * sizeof(double) * ns,
+                                 cudaMemcpyDeviceToHost, b->ms));
+    CPM_CUDA_TRY(cudaStreamSynchronize(b->ms));
+    if (ci < cand.size()) {
+      float ms = 0.f;
+      CPM_CUDA_TRY(cudaEventElapsedTime(&ms, b->t0, b->t1));
+      int slot = 0;
+      while ((1 << slot) < K && slot < 7) ++slot;
+      b->tune_ms[slot] = ms;
+      if (ms < best_ms) { best_ms = ms; best_k = K; }
+      if (++ci == cand.size()) {
+        b->chosen = best_k;
+        cache_store(*b, best_k);
+      }
+    }
+    for (int s : in_graph) rel[s] = b->host_norms[4 * (size_t)s] / fmax[s];
+  }
+  if (result != CPM_OK)
+    for (int s = 0; s < ns; ++s)
+      if (!done[s])
+        CPM_CUDA_TRY(cudaMemcpyAsync(u[s], b->W[s]->u_own.get(), b->H[s]->L[0].lev->nB * sizeof(double),
+                                     cudaMemcpyDeviceToDevice, b->ms));
+  if (b->chosen == 0 && best_k > 0) b->chosen = best_k;
+  CPM_CUDA_TRY(cudaEventRecord(b->ev_fork, b->ms));
+  CPM_CUDA_TRY(cudaStreamWaitEvent(us, b->ev_fork, 0));
+  CPM_CUDA_TRY(cudaStreamSynchronize(b->ms));
+  const double secs = std::chrono::duration<double>(std::chrono::steady_clock::now() - tstart).count();
+  if (reports)
+    for (int s = 0; s < ns; ++s) {
+      rep[s].seconds = secs;
+      reports[s] = rep[s];
+    }
+  if (result != CPM_OK) {
+    cpm::set_last_error(result == CPM_ERR_DIVERGED ? "a system of the batch diverged"
+                                                   : "max_iter reached before every system converged");
+    return result;
+  }
+  CPM_API_END
+}
+
+cpm_status cpm_batch_info(cpm_batch b, int32_t* concurrency, double* tune_ms) {
+  CPM_API_BEGIN
+  CPM_CHECK(b != nullptr, CPM_ERR_ARG, "NULL argument");
+  if (concurrency) *concurrency = b->chosen;
+  if (tune_ms)
+    for (int q = 0; q < 8; ++q) tune_ms[q] = b->tune_ms[q];
+  CPM_API_END
+}
+
+cpm_status cpm_batch_destroy(cpm_batch b) {
+  CPM_API_BEGIN
+  delete b;
   CPM_API_END
 }
 

@@ -199,6 +199,59 @@ class Hierarchy:
             pass
 
 
+def _report(st, rep) -> dict:
+    n = min(rep.iters + 1, capi.CPM_MAX_HISTORY)
+    return {"status": st, "iters": rep.iters, "converged": bool(rep.converged),
+            "rel_residual": rep.rel_residual, "history": list(rep.history[:n]),
+            "seconds": rep.seconds}
+
+
+class Batch:
+    """Independent systems A_i u = f over several hierarchies (cpm_build_batch).
+
+    System ``s = i * n_rhs + k`` uses ``hiers[i]``; every system has its own
+    workspace.  The hierarchies must outlive the batch.
+    """
+
+    def __init__(self, hiers: list[Hierarchy], n_rhs: int = 1, tune_cache: str | None = None):
+        self.hiers = list(hiers)
+        self.n_rhs = n_rhs
+        self.sizes = [h.nb for h in self.hiers for _ in range(n_rhs)]
+        self.handle = capi.cpm_build_batch([h.handle for h in self.hiers], n_rhs, tune_cache)
+
+    def solve(self, fs: list[torch.Tensor], us: list[torch.Tensor] | None = None, tol: float = 1e-10,
+              max_iter: int = 100, mode: str = "mixed", inner_cycles: int = 1,
+              zero_init: bool | None = None, stream=None, raise_on_fail: bool = True):
+        if len(fs) != len(self.sizes):
+            raise ValueError(f"expected {len(self.sizes)} right-hand sides")
+        zero = us is None if zero_init is None else bool(zero_init)
+        if us is None:
+            us = [torch.empty_like(f) for f in fs]
+        o = capi.cpm_solve_opts()
+        o.tol, o.max_iter = tol, max_iter
+        o.mode = capi.CPM_SOLVE_MIXED if mode == "mixed" else capi.CPM_SOLVE_F64
+        o.use_graph, o.zero_init, o.inner_cycles, o.learned = 1, int(zero), inner_cycles, 0
+        fp = [_ptr(f, torch.float64, n) for f, n in zip(fs, self.sizes)]
+        up = [_ptr(u, torch.float64, n) for u, n in zip(us, self.sizes)]
+        st, reps = capi.cpm_solve_batch(self.handle, fp, up, o, _stream(stream), raise_on_fail)
+        return us, [_report(st, r) for r in reps]
+
+    def info(self):
+        """(concurrency chosen by the autotuner, ms of one iteration per K = 1, 2, 4, ...)."""
+        return capi.cpm_batch_info(self.handle)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            capi.cpm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
 class Smoother:
     """Learned smoother network (cpm_mlp): parameters live on the device."""
 

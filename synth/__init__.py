@@ -18,6 +18,10 @@ Workloads (shapes of the paper's experiments, Sec. 3.4 and Sec. 4.5):
 * ``u_rand``  a smooth field sum_{j=1..8} prod_{a} sin(k_{j,a} y_a + phi_{j,a}),
   k_j integer vectors, 0 < |k_j| <= 4 (rejection sampling), phi ~ U[0, 2 pi).
 * ``random_band_vector``  uniform [-1, 1) values (operator parity tests).
+* ``ellipsoid_batch``  the batched workload: semi-axes ~ U[0.6, 1.2]^3 and a
+  spacing drawn from {1/64, 1/96, 1/128} per instance.
+* ``harmonic_field``  sum a_lm Y_lm(y / |y|) over l in {2, 3, 5} (a
+  spherical-harmonic-like right-hand side on any star-shaped surface).
 """
 from __future__ import annotations
 
@@ -148,3 +152,21 @@ def variable_c(y: np.ndarray) -> np.ndarray:
 
 def random_band_vector(n: int, seed: int = 0) -> np.ndarray:
     return np.random.default_rng(seed).uniform(-1.0, 1.0, size=n)
+
+
+def ellipsoid_batch(seed: int = 0, count: int = 64, lo: float = 0.6, hi: float = 1.2,
+                    spacings=(1 / 64, 1 / 96, 1 / 128)):
+    """[(semi-axes (a, b, c), dx)] for ``count`` instances."""
+    rng = np.random.default_rng(seed)
+    axes = rng.uniform(lo, hi, size=(count, 3))
+    pick = rng.integers(0, len(spacings), size=count)
+    return [(tuple(float(v) for v in axes[i]), float(spacings[pick[i]])) for i in range(count)]
+
+
+def harmonic_field(y: np.ndarray, seed: int = 0, degrees=SPHERE_DEGREES) -> np.ndarray:
+    """sum a_lm Y_lm(y / |y|), a_lm ~ N(0, 1) from the seed."""
+    d = y / np.linalg.norm(y, axis=1, keepdims=True)
+    out = np.zeros(y.shape[0])
+    for l, m, a in sphere_coefficients(seed, degrees):
+        out += a * real_sph_harm(l, m, d)
+    return out
