@@ -375,7 +375,7 @@ def run_cpm(args, world, rank, local):
            if not args.no_cpu_baseline and args.workload == "sphere256" else None)
     nl = H.n_levels
     sizes = [H.level_size(l) for l in range(nl)]
-    sweeps = 6
+    sweeps = 2 * args.nu * args.inner  # Jacobi sweeps per level per outer iteration
     updates = sum(sizes[:-1]) * sweeps * iters_mixed
     line = {
         "metric": METRIC, "value": mixed_ms / 1e3, "unit": "s", "n_gpus": world,
@@ -410,6 +410,100 @@ def run_cpm(args, world, rank, local):
             "sample": f"oracle FP64 solve of the unit sphere at dx=1/64 ({cpu['nb_sample']} points) "
                       f"to 1e-10 in {cpu['sample_s']:.2f} s, scaled x{cpu['scale']:.2f} to dx=1/256"}
     print(json.dumps(line), flush=True)
+
+
+def run_batch(args, world, rank, local):
+    """Batched workload: 64 ellipsoids (semi-axes ~ U[0.6, 1.2]^3, dx drawn from
+    {1/64, 1/96, 1/128}) x 4 right-hand sides, all solved to 1e-10 by one
+    cpm_solve_batch call (one graph launch per outer iteration, autotuned
+    concurrency).  The same systems solved one after another with cpm_solve are
+    timed beside it."""
+    import numpy as np
+    import torch
+
+    import paper_1307_4354_gb300 as pkg
+    import synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pkg.build()
+    inst = synth.ellipsoid_batch(seed=0, count=args.batch_count)
+    n_rhs = 4
+    t0 = time.perf_counter()
+    hs, fs = [], []
+    for i, (ax, dx) in enumerate(inst):
+        g = pkg.Band("ellipsoid", ax, dx)
+        H = pkg.Hierarchy(g, nu1=args.nu, nu2=args.nu, omega=args.omega, residual=args.residual,
+                          coarse_f64_max=4096, coarse_dense_max=65536)
+        _, cp, _ = g.export()
+        for fk in synth.harmonic_fields(cp[: g.nb], [100 * i + k for k in range(n_rhs)]):
+            fs.append(torch.from_numpy(fk).to(dev))
+        hs.append(H)
+        del g
+    B = pkg.Batch(hs, n_rhs)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    us = [torch.zeros_like(f) for f in fs]
+    st = torch.cuda.current_stream()
+
+    def solve():
+        _, reps = B.solve(fs, us, tol=1e-10, max_iter=200, mode="mixed", inner_cycles=args.inner,
+                          zero_init=True, raise_on_fail=False)
+        return reps
+
+    for _ in range(args.warmup):  # the first solve also runs the autotuner
+        solve()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    launches0 = pkg.capi.cpm_kernel_launches()
+    with ClockSampler(local) as clk:
+        torch.cuda.synchronize()
+        ev0.record(st)
+        reps = [solve() for _ in range(args.steps)]
+        ev1.record(st)
+        torch.cuda.synchronize()
+    batch_ms = ev0.elapsed_time(ev1) / args.steps
+    launches = pkg.capi.cpm_kernel_launches() - launches0
+    last = reps[-1]
+    # the same systems one after another (cpm_solve per system)
+    torch.cuda.synchronize()
+    ev0.record(st)
+    seq_iters = []
+    for s, f in enumerate(fs):
+        _, r = hs[s // n_rhs].solve(f, us[s], tol=1e-10, max_iter=200, mode="mixed",
+                                    inner_cycles=args.inner, zero_init=True, raise_on_fail=False)
+        seq_iters.append(r["iters"])
+    ev1.record(st)
+    torch.cuda.synchronize()
+    seq_ms = ev0.elapsed_time(ev1)
+    K, tune = B.info()
+    iters = [r["iters"] for r in last]
+    sizes = [h.nb for h in hs]
+    coarse = [h.level_size(h.n_levels - 1) for h in hs]
+    pts = sum(sizes) * n_rhs
+    if rank != 0:
+        return
+    line = {
+        "metric": "s to 1e-10 rel residual, batch of 64 ellipsoids x 4 RHS (mixed FP32/FP64)",
+        "value": batch_ms / 1e3, "unit": "s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": batch_ms, "higher_is_better": False,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": f"{len(hs)} ellipsoids, semi-axes U[0.6,1.2]^3 (seed 0), dx in "
+                               "{1/64,1/96,1/128}, 4 harmonic right-hand sides each, c=1, tol 1e-10",
+                   "band_points": sizes, "coarsest_points": coarse, "inner_cycles": args.inner,
+                   "smoother": f"jacobi nu={args.nu}/{args.nu} omega={args.omega}",
+                   "residual": args.residual, "l2": "inputs larger than L2 (no flush)"},
+        "systems": len(fs), "points_x_rhs": pts,
+        "converged": sum(1 for r in last if r["converged"]),
+        "status": sorted({r["status"] for r in last}),
+        "iters": {"min": min(iters), "max": max(iters), "mean": float(np.mean(iters))},
+        "autotune": {"concurrency": K, "ms_per_iteration_by_K": tune},
+        "sequential_s": seq_ms / 1e3, "sequential_iters_equal": seq_iters == iters,
+        "band_point_updates_per_s": sum(sizes[s // n_rhs] * iters[s] for s in range(len(fs)))
+        * 2 * args.inner * args.nu / (batch_ms * 1e-3),
+        "setup_s": setup_s, "gpu_launches": int(launches), "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    B.close()
 
 
 def run_micro(args):
@@ -469,6 +563,9 @@ def main():
     ap.add_argument("--only-mixed", action="store_true",
                     help="time only the mixed-precision solve (profiling runs)")
     ap.add_argument("--train-steps", type=int, default=400)
+    ap.add_argument("--batch", action="store_true",
+                    help="batched workload: ellipsoids x 4 right-hand sides in one cpm_solve_batch")
+    ap.add_argument("--batch-count", type=int, default=64, help="ellipsoids in the batched workload")
     ap.add_argument("--omega", type=float, default=0.8, help="Jacobi weight")
     ap.add_argument("--micro", default=None,
                     help="kernel micro-benchmark instead of the solve: extend32|extend64|apply32|apply64|all")
@@ -476,6 +573,9 @@ def main():
     world, rank, local = dist_setup()
     if args.micro:
         run_micro(args)
+        return
+    if args.batch:
+        run_batch(args, world, rank, local)
         return
     if args.impl == "reference":
         run_reference(args, world, rank)

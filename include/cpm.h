@@ -129,8 +129,15 @@ typedef enum cpm_smoother {
 typedef enum cpm_prec { CPM_F64 = 0, CPM_F32 = 1 } cpm_prec;
 
 typedef struct cpm_mg_opts {
-  double coarsest_dx;   /* spacing of the coarsest level (0: coarsen while
-                           (sqrt(lambda2)+1)*dx < reach and |B| > 64)           */
+  double coarsest_dx;   /* spacing of the coarsest level.  0: coarsen while
+                           (sqrt(lambda2)+1)*dx < reach and |B| > 64, so that cp
+                           is unique on B+ of every level; then, only while the
+                           coarsest level is larger than coarse_dense_max, add
+                           levels whose band half-width sqrt(lambda2)*dx stays
+                           below the reach and whose band builds (cp defined on
+                           B+, every stencil inside the band).  > 0: levels
+                           down to that spacing, each with
+                           sqrt(lambda2)*dx < reach (CPM_ERR_REACH otherwise)  */
   int32_t nu1, nu2;     /* pre / post smoothing sweeps (0: 3 and 3)             */
   double omega;         /* Jacobi weight (0: 0.8)                               */
   int32_t smoother;     /* cpm_smoother                                         */
@@ -142,10 +149,14 @@ typedef struct cpm_mg_opts {
   int32_t residual_mode;  /* residual restricted by the Jacobi V-cycle:
                              0: f - A (E u) (Sec. 4.4), 1: f - A u              */
   int32_t coarse_sweeps;  /* coarsest level: 0 = direct solve by an explicit
-                             inverse, FP64 (Gauss-Jordan) up to 16384 points,
-                             FP32 (library LU at setup, FP64 refinement in FP64
-                             V-cycles) up to 40000, else 40 Jacobi sweeps;
+                             inverse, FP64 (Gauss-Jordan) up to coarse_f64_max
+                             points, FP32 (library LU at setup, two FP64
+                             refinement steps in FP64 V-cycles) up to
+                             coarse_dense_max, else 40 Jacobi sweeps;
                              > 0 = that many Jacobi sweeps                      */
+  int32_t coarse_f64_max;   /* 0: 16384 (the FP64 inverse costs 8 n^2 bytes)   */
+  int32_t coarse_dense_max; /* 0: 40000 (the FP32 inverse costs 4 n^2 bytes);
+                               at most 65536                                    */
 } cpm_mg_opts;
 
 typedef struct cpm_hier_s* cpm_hier;

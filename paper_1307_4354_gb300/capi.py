@@ -36,7 +36,8 @@ class cpm_mg_opts(C.Structure):
     _fields_ = [("coarsest_dx", C.c_double), ("nu1", C.c_int32), ("nu2", C.c_int32),
                 ("omega", C.c_double), ("smoother", C.c_int32), ("transfer_deg", C.c_int32),
                 ("c", C.c_double), ("c_device", C.c_void_p), ("residual_mode", C.c_int32),
-                ("coarse_sweeps", C.c_int32)]
+                ("coarse_sweeps", C.c_int32), ("coarse_f64_max", C.c_int32),
+                ("coarse_dense_max", C.c_int32)]
 
 
 class cpm_solve_opts(C.Structure):
@@ -212,7 +213,7 @@ def cpm_solve(h: int, f_ptr: int, u_ptr: int, opts: cpm_solve_opts, stream: int 
     rep = cpm_solve_report()
     st = lib().cpm_solve(C.c_void_p(h), C.c_void_p(f_ptr), C.c_void_p(u_ptr), C.byref(opts),
                          C.byref(rep), C.c_void_p(stream))
-    if raise_on_fail:
+    if raise_on_fail or st not in (CPM_OK, CPM_ERR_NOT_CONVERGED, CPM_ERR_DIVERGED):
         _check(st, "cpm_solve")
     return st, rep
 
@@ -299,7 +300,7 @@ def cpm_solve_batch(b: int, f_ptrs: list[int], u_ptrs: list[int], opts: cpm_solv
     ua = (C.c_void_p * n)(*u_ptrs)
     reps = (cpm_solve_report * n)()
     st = lib().cpm_solve_batch(C.c_void_p(b), fa, ua, C.byref(opts), reps, C.c_void_p(stream))
-    if raise_on_fail:
+    if raise_on_fail or st not in (CPM_OK, CPM_ERR_NOT_CONVERGED, CPM_ERR_DIVERGED):
         _check(st, "cpm_solve_batch")
     return st, list(reps)
 

@@ -7,7 +7,9 @@
 // steps of iterative refinement with the FP64 residual (hier.cu).
 #include <cusolverDn.h>
 
+
 #include "ops.cuh"
+#include "gemv.cuh"
 
 namespace cpm {
 
@@ -54,45 +56,14 @@ void invert_dense_f32(float* A, float* X, int32_t n, cudaStream_t st, int32_t* e
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
-// x (+)= Ainv b with an FP32 matrix: b staged in shared memory as FP32, one
-// warp per row, FP32 accumulation.
-constexpr int kGemv32Threads = 512;
-template <typename T, bool ADD>
-__global__ void __launch_bounds__(kGemv32Threads) k_coarse_gemv32(const float* __restrict__ Ainv,
-                                                                  const T* __restrict__ b,
-                                                                  T* __restrict__ x, int32_t n) {
-  extern __shared__ float sb32[];
-  for (int32_t j = threadIdx.x; j < n; j += blockDim.x) sb32[j] = (float)b[j];
-  __syncthreads();
-  const int32_t row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
-  const float* a = Ainv + (size_t)row * n;
-  float s = 0.f;
-  for (int32_t j = lane; j < n; j += 32) s += __ldg(a + j) * sb32[j];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) x[row] = ADD ? x[row] + (T)s : (T)s;
-}
-
-void init_coarse_gemv32() {
-  CPM_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv32<double, false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  CPM_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv32<double, true>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-  CPM_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv32<float, false>,
-                                    cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-}
-
+// x (+)= Ainv b with the FP32 inverse (chunked dense product, FP32 accumulation).
 template <typename T>
 void launch_coarse_gemv32(const float* Ainv, const T* b, T* x, int32_t n, bool add, cudaStream_t st) {
-  const size_t smem = (size_t)n * sizeof(float);
-  const unsigned grid = nblk((int64_t)n * 32, kGemv32Threads);
   if (add) {
     if constexpr (sizeof(T) == 8)
-      k_coarse_gemv32<T, true><<<grid, kGemv32Threads, smem, st>>>(Ainv, b, x, n);
+      k_dense_gemv<float, T, true><<<dense_gemv_blocks(n), kGemvWarps * 32, 0, st>>>(Ainv, b, x, n);
   } else {
-    k_coarse_gemv32<T, false><<<grid, kGemv32Threads, smem, st>>>(Ainv, b, x, n);
+    k_dense_gemv<float, T, false><<<dense_gemv_blocks(n), kGemvWarps * 32, 0, st>>>(Ainv, b, x, n);
   }
   count_launch();
 }

@@ -550,6 +550,10 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
   const Level& f0 = finest->lev;
   const double reach = surface_reach(finest->surface);
   const double lam = std::sqrt(f0.lambda2);
+  CPM_CHECK(o.coarse_f64_max >= 0 && o.coarse_dense_max >= 0 && o.coarse_dense_max <= 65536,
+            CPM_ERR_ARG, "bad coarse_f64_max / coarse_dense_max");
+  const int64_t dense_max = o.coarse_dense_max > 0 ? o.coarse_dense_max : 40000;
+  const int64_t f64_max = std::min<int64_t>(o.coarse_f64_max > 0 ? o.coarse_f64_max : 16384, dense_max);
 
   // levels
   H->L.emplace_back();
@@ -562,7 +566,7 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
     bool more;
     if (o.coarsest_dx > 0) {
       more = next <= o.coarsest_dx * (1 + 1e-12);
-      CPM_CHECK(!more || (lam + 1.0) * next < reach, CPM_ERR_REACH,
+      CPM_CHECK(!more || lam * next < reach, CPM_ERR_REACH,
                 "coarsest_dx too coarse for the surface reach");
     } else {
       more = (lam + 1.0) * next < reach && cur.nB > 64;
@@ -576,15 +580,34 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
     build_level(finest->surface, f0.lo, next, n_next, f0.lambda2, st, *H->L.back().lev);
     dx = next;
   }
+  if (!(o.coarsest_dx > 0)) {
+    // a coarsest level too large for the dense solve: coarser levels whose
+    // band stays within the reach, as long as their band builds
+    while (H->L.back().lev->nB > dense_max && lam * 2.0 * dx < reach) {
+      const double next = 2.0 * dx;
+      const int n_next = (int)std::llround(-2.0 * f0.lo / next) + 1;
+      if (std::fabs((n_next - 1) * next + 2.0 * f0.lo) >= 1e-9 * next) break;
+      std::unique_ptr<Level> lv(new Level);
+      try {
+        build_level(finest->surface, f0.lo, next, n_next, f0.lambda2, st, *lv);
+      } catch (const Error& e) {
+        if (e.status != CPM_ERR_REACH) throw;
+        break;
+      }
+      H->L.emplace_back();
+      H->L.back().lev = std::move(lv);
+      dx = next;
+    }
+  }
   const int nl = (int)H->L.size();
   const Level& cl = *H->L[nl - 1].lev;
   CPM_CHECK(o.coarse_sweeps >= 0 && o.coarse_sweeps <= 10000, CPM_ERR_ARG, "bad coarse_sweeps");
   if (o.coarse_sweeps > 0) {
     H->coarse_mode = 2;
     H->coarse_sweeps = o.coarse_sweeps;
-  } else if (cl.nB <= 16384) {
+  } else if (cl.nB <= f64_max) {
     H->coarse_mode = 0;
-  } else if (cl.nB <= 40000) {
+  } else if (cl.nB <= dense_max) {
     H->coarse_mode = 1;
   } else {
     H->coarse_mode = 2;
@@ -627,7 +650,6 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
     CPM_CUDA_TRY(cudaStreamSynchronize(st));
     lv.dM64 = std::move(dM);
   }
-  init_coarse_gemv();
   // coarsest: dense A = diag(c) - M, inverted in place (FP64)
   H->nc = cl.nB;
   const size_t nn = (size_t)H->nc * H->nc;
@@ -639,7 +661,6 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
     CPM_CUDA_TRY(cudaGetLastError());
     invert_dense(H->Ainv.get(), H->nc, st, err.get());
   } else if (H->coarse_mode == 1) {
-    init_coarse_gemv32();
     DBuf<float> A32(nn);
     CPM_CUDA_TRY(cudaMemsetAsync(A32.get(), 0, sizeof(float) * nn, st));
     launch_assemble_A<float>(H->L[nl - 1].view<double>(), H->L[nl - 1].c64.get(), H->c, A32.get(),

@@ -6,6 +6,7 @@
 #include <cmath>
 
 #include "ops.cuh"
+#include "gemv.cuh"
 
 #include <atomic>
 
@@ -287,38 +288,10 @@ void launch_cast_from_f64(const double* x, T* y, int64_t n, cudaStream_t st) {
 }
 
 // ----------------------------------------------------------------- coarse solve
-// x = Ainv b: b staged once per CTA in shared memory as FP64, one warp per
-// row, FP64 accumulation.
-constexpr int kGemvThreads = 512;
-template <typename T>
-__global__ void __launch_bounds__(kGemvThreads) k_coarse_gemv(const double* __restrict__ Ainv,
-                                                              const T* __restrict__ b,
-                                                              T* __restrict__ x, int32_t n) {
-  extern __shared__ double sb[];
-  for (int32_t j = threadIdx.x; j < n; j += blockDim.x) sb[j] = (double)b[j];
-  __syncthreads();
-  const int32_t row = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  const int lane = threadIdx.x & 31;
-  if (row >= n) return;
-  const double* a = Ainv + (size_t)row * n;
-  double s = 0.0;
-  for (int32_t j = lane; j < n; j += 32) s += __ldg(a + j) * sb[j];
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (lane == 0) x[row] = (T)s;
-}
-
-void init_coarse_gemv() {
-  CPM_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    16384 * 8));
-  CPM_CUDA_TRY(cudaFuncSetAttribute(k_coarse_gemv<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                    16384 * 8));
-}
-
+// x = Ainv b with the FP64 inverse (chunked dense product, FP64 accumulation).
 template <typename T>
 void launch_coarse_gemv(const double* Ainv, const T* b, T* x, int32_t n, cudaStream_t st) {
-  const size_t smem = (size_t)n * sizeof(double);
-  k_coarse_gemv<T><<<nblk((int64_t)n * 32, kGemvThreads), kGemvThreads, smem, st>>>(Ainv, b, x, n);
+  k_dense_gemv<double, T, false><<<dense_gemv_blocks(n), kGemvWarps * 32, 0, st>>>(Ainv, b, x, n);
   count_launch();
 }
 

@@ -87,9 +87,7 @@ void launch_cast_to_f64(const T* x, double* y, int64_t n, cudaStream_t st);
 template <typename T>
 void launch_cast_from_f64(const double* x, T* y, int64_t n, cudaStream_t st);
 
-// Coarsest direct solve x = Ainv b (FP64 matrix, FP64 accumulation);
-// init_coarse_gemv() raises the kernel's shared-memory limit (once, at setup).
-void init_coarse_gemv();
+// Coarsest direct solve x = Ainv b (FP64 matrix, FP64 accumulation).
 template <typename T>
 void launch_coarse_gemv(const double* Ainv, const T* b, T* x, int32_t n, cudaStream_t st);
 
@@ -99,7 +97,6 @@ void residual_norms_noalloc(const LevelView<double>& v, const double* f, const d
                             const double* cvec, double cval, double* norms, cudaStream_t st);
 
 // Coarsest solve with an FP32 explicit inverse (coarse32.cu): x (+)= Ainv b.
-void init_coarse_gemv32();
 template <typename T>
 void launch_coarse_gemv32(const float* Ainv, const T* b, T* x, int32_t n, bool add, cudaStream_t st);
 // A (row-major FP32, overwritten) -> X = A^-1 (library LU, setup only).

@@ -82,12 +82,14 @@ class Hierarchy:
     def __init__(self, band: Band, coarsest_dx: float = 0.0, nu1: int = 3, nu2: int = 3,
                  omega: float = 0.8, smoother: str = "jacobi", c: float = 1.0,
                  c_device: torch.Tensor | None = None, residual: str = "extended",
-                 coarse_sweeps: int = 0, stream=None):
+                 coarse_sweeps: int = 0, coarse_f64_max: int = 0, coarse_dense_max: int = 0,
+                 stream=None):
         o = capi.cpm_mg_opts()
         o.coarsest_dx, o.nu1, o.nu2, o.omega = coarsest_dx, nu1, nu2, omega
         o.smoother, o.transfer_deg, o.c = _SMOOTHERS[smoother], 1, c
         o.residual_mode = {"extended": capi.CPM_RESID_EXTENDED, "plain": capi.CPM_RESID_PLAIN}[residual]
         o.coarse_sweeps = coarse_sweeps
+        o.coarse_f64_max, o.coarse_dense_max = coarse_f64_max, coarse_dense_max
         o.c_device = _ptr(c_device, torch.float64, band.nb) if c_device is not None else None
         self.band = band
         self.handle = capi.cpm_build_hierarchy(band.handle, o, _stream(stream))

@@ -165,8 +165,12 @@ def ellipsoid_batch(seed: int = 0, count: int = 64, lo: float = 0.6, hi: float =
 
 def harmonic_field(y: np.ndarray, seed: int = 0, degrees=SPHERE_DEGREES) -> np.ndarray:
     """sum a_lm Y_lm(y / |y|), a_lm ~ N(0, 1) from the seed."""
+    return harmonic_fields(y, [seed], degrees)[0]
+
+
+def harmonic_fields(y: np.ndarray, seeds, degrees=SPHERE_DEGREES) -> list[np.ndarray]:
+    """``harmonic_field`` for several seeds (the harmonics evaluated once)."""
     d = y / np.linalg.norm(y, axis=1, keepdims=True)
-    out = np.zeros(y.shape[0])
-    for l, m, a in sphere_coefficients(seed, degrees):
-        out += a * real_sph_harm(l, m, d)
-    return out
+    lm = [(l, m) for l in degrees for m in range(-l, l + 1)]
+    Y = np.stack([real_sph_harm(l, m, d) for l, m in lm], axis=1)
+    return [Y @ np.array([a for _, _, a in sphere_coefficients(s, degrees)]) for s in seeds]

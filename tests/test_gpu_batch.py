@@ -82,6 +82,7 @@ def test_batch_reports_non_convergence_and_rejects_bad_input():
     o = pkg.capi.cpm_solve_opts()
     o.tol, o.max_iter, o.mode, o.learned = 1e-10, 10, pkg.capi.CPM_SOLVE_MIXED, 1
     ptrs = [f.data_ptr() for f in fs]
-    st, _ = pkg.capi.cpm_solve_batch(B.handle, ptrs, ptrs, o, 0, raise_on_fail=False)
-    assert st == pkg.capi.CPM_ERR_ARG
+    with pytest.raises(pkg.capi.CpmError) as e:
+        pkg.capi.cpm_solve_batch(B.handle, ptrs, ptrs, o, 0, raise_on_fail=False)
+    assert e.value.status == pkg.capi.CPM_ERR_ARG
     B.close()

@@ -128,3 +128,31 @@ def test_vcycle_parity_large_coarsest_level():
     u = torch.zeros(nb, dtype=torch.float64, device="cuda")
     H.vcycle(torch.from_numpy(f_o[perm]).cuda(), u)
     assert np.abs(u.cpu().numpy() - ref).max() <= 1e-9 * np.abs(ref).max()
+
+
+def test_vcycle_parity_relaxed_coarse_level():
+    """Ellipsoid (1.05, 0.9, 0.8), reach 0.61: the level dx = 1/8 has a band
+    within the reach (sqrt(17)/8 = 0.52) but not its ghost ring margin
+    ((sqrt(17)+1)/8 = 0.64).  It builds (cp is defined on all of B+), the GPU
+    V-cycle matches the oracle's on it, and auto coarsening takes it only when
+    the coarsest strict level is too large for the dense solve."""
+    torch, pkg, g, H, OH, perm = _hier_pair("ellipsoid", (1.05, 0.9, 0.8), 1 / 16, coarsest=1 / 8)
+    nb = OH.fine.band.nb
+    assert H.n_levels == 2 and H.level_size(1) == OH.levels[1].band.nb
+    f_o = synth.random_band_vector(nb, 21)
+    ref = vcycle(OH, np.zeros(nb), f_o)[perm]
+    u = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    H.vcycle(torch.from_numpy(f_o[perm]).cuda(), u)
+    assert np.abs(u.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+    _, rep = H.solve(torch.from_numpy(f_o[perm]).cuda(), tol=1e-10, mode="mixed")
+    assert rep["converged"] and rep["iters"] <= 12, rep
+    # auto: the strict rule stops at dx = 1/16; with a dense limit below |B(1/16)|
+    # the relaxed level dx = 1/8 is added
+    Ha = pkg.Hierarchy(g, coarse_dense_max=8192)
+    assert Ha.n_levels == 2 and Ha.level_size(1) == H.level_size(1)
+    Hs = pkg.Hierarchy(g)
+    assert Hs.n_levels == 1
+    # an explicit spacing whose band leaves the reach is refused
+    with pytest.raises(pkg.capi.CpmError) as e:
+        pkg.Hierarchy(g, coarsest_dx=1 / 4)
+    assert e.value.status == pkg.capi.CPM_ERR_REACH
