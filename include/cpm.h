@@ -337,10 +337,14 @@ cpm_status cpm_build_batch(const cpm_hier* hiers, int32_t n_hier, int32_t n_rhs,
  * f[s], u[s]: host arrays of n_hier * n_rhs device pointers to FP64 vectors of
  * length |B_0| of system s's hierarchy (caller-owned); u[s] is the initial
  * guess unless opts->zero_init.  Each outer iteration of all active systems is
- * one launch of a CUDA graph in which the systems run on K concurrent
- * branches, largest first; the autotuner picks K: the first outer iterations
- * try K = 1, 2, 4, ..., min(32, systems), each a real iteration, and keep the
- * fastest (stored in the tune cache; read from it when present).  After each
+ * one launch of a CUDA graph.  Systems of the same hierarchy form lockstep
+ * groups (up to 16): one stream issues every V-cycle step for each member in
+ * turn and the coarsest direct solve reads the dense inverse once for up to 4
+ * members.  The groups run on K concurrent branches (largest first, each to
+ * the least loaded branch); the autotuner picks K: the first outer iterations
+ * try K = 1, 2, 4, ..., min(32, groups), each a real iteration, and keep the
+ * fastest (stored in the tune cache; read from it when present).  Each
+ * system's arithmetic is that of cpm_solve, bit for bit.  After each
  * launch the host reads every system's residual norm.  A system's result is
  * its first iterate with ||f - A u||_inf / ||f||_inf <= tol (the same iterate
  * cpm_solve returns); its workspace may keep iterating inside the graph until

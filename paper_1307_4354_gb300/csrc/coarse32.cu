@@ -56,21 +56,21 @@ void invert_dense_f32(float* A, float* X, int32_t n, cudaStream_t st, int32_t* e
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
 }
 
-// x (+)= Ainv b with the FP32 inverse (chunked dense product, FP32 accumulation).
+// x_g (+)= Ainv b_g with the FP32 inverse (chunked dense product, FP32 accumulation).
 template <typename T>
-void launch_coarse_gemv32(const float* Ainv, const T* b, T* x, int32_t n, bool add, cudaStream_t st) {
+void launch_coarse_gemv32(const float* Ainv, const T* const* b, T* const* x, int G, int32_t n, bool add,
+                          cudaStream_t st) {
   if (add) {
-    if constexpr (sizeof(T) == 8)
-      k_dense_gemv<float, T, true><<<dense_gemv_blocks(n), kGemvWarps * 32, 0, st>>>(Ainv, b, x, n);
+    if constexpr (sizeof(T) == 8) launch_dense_gemv<float, T, true>(Ainv, b, x, G, n, st);
   } else {
-    k_dense_gemv<float, T, false><<<dense_gemv_blocks(n), kGemvWarps * 32, 0, st>>>(Ainv, b, x, n);
+    launch_dense_gemv<float, T, false>(Ainv, b, x, G, n, st);
   }
-  count_launch();
+  count_launch((G + kGemvMaxVectors - 1) / kGemvMaxVectors);
 }
 
-template void launch_coarse_gemv32<double>(const float*, const double*, double*, int32_t, bool,
-                                           cudaStream_t);
-template void launch_coarse_gemv32<float>(const float*, const float*, float*, int32_t, bool,
-                                          cudaStream_t);
+template void launch_coarse_gemv32<double>(const float*, const double* const*, double* const*, int,
+                                           int32_t, bool, cudaStream_t);
+template void launch_coarse_gemv32<float>(const float*, const float* const*, float* const*, int, int32_t,
+                                          bool, cudaStream_t);
 
 }  // namespace cpm

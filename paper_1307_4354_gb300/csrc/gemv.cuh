@@ -1,9 +1,10 @@
-// Dense matrix-vector product x (+)= A b for the explicit inverse of the
-// coarsest-level matrix (row-major n x n, FP64 or FP32).  HBM-bound: each
-// warp streams kGemvRowsPerWarp rows with coalesced loads (independent loads
-// in flight per lane), and b passes through shared memory in chunks shared by
-// the block's 64 rows, so the staging needs no more than 16 KB whatever n is.
-// Accumulation in the matrix type; fixed summation order.
+// Dense matrix-vector products x (+)= A b for the explicit inverse of the
+// coarsest-level matrix (row-major n x n, FP64 or FP32), for one or several
+// right-hand sides at once.  HBM-bound on A: each warp streams
+// kGemvRowsPerWarp rows with coalesced loads (independent loads in flight per
+// lane), and the vectors pass through shared memory in chunks shared by the
+// block's 64 rows (32 KB at most, whatever n is).  Accumulation in the matrix
+// type; fixed summation order.
 #pragma once
 #include <cstdint>
 
@@ -12,48 +13,92 @@ namespace cpm {
 constexpr int kGemvWarps = 16;
 constexpr int kGemvRowsPerWarp = 4;
 constexpr int kGemvRowsPerBlock = kGemvWarps * kGemvRowsPerWarp;
-constexpr int kGemvChunk = 2048;
+constexpr int kGemvMaxVectors = 4;
 
-template <typename M, typename T, bool ADD>
+// Up to kGemvMaxVectors right-hand sides that share the matrix: each matrix
+// element is read once and multiplied into every vector.
+template <typename T>
+struct GemvVectors {
+  const T* b[kGemvMaxVectors];
+  T* x[kGemvMaxVectors];
+};
+
+// Each lane accumulates the columns j = lane (mod 32) in increasing order, so
+// the result of one vector does not depend on NV or on the chunk size (a
+// multiple of 32).
+template <typename M, typename T, bool ADD, int NV>
 __global__ void __launch_bounds__(kGemvWarps * 32) k_dense_gemv(const M* __restrict__ A,
-                                                                const T* __restrict__ b,
-                                                                T* __restrict__ x, int32_t n) {
-  __shared__ M sb[kGemvChunk];
+                                                                GemvVectors<T> v, int32_t n) {
+  constexpr int kChunk = (4096 / NV) / 32 * 32;  // a multiple of 32
+  __shared__ M sb[NV][kChunk];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int32_t row0 = blockIdx.x * kGemvRowsPerBlock + warp * kGemvRowsPerWarp;
   const M* a[kGemvRowsPerWarp];
   bool ok[kGemvRowsPerWarp];
-  M acc[kGemvRowsPerWarp];
+  M acc[kGemvRowsPerWarp][NV];
 #pragma unroll
   for (int r = 0; r < kGemvRowsPerWarp; ++r) {
     ok[r] = row0 + r < n;
     a[r] = A + (size_t)(ok[r] ? row0 + r : 0) * n;
-    acc[r] = M(0);
-  }
-  for (int32_t c0 = 0; c0 < n; c0 += kGemvChunk) {
-    const int32_t cn = min(kGemvChunk, n - c0);
-    __syncthreads();
-    for (int32_t j = threadIdx.x; j < cn; j += blockDim.x) sb[j] = (M)b[c0 + j];
-    __syncthreads();
-#pragma unroll 4
-    for (int32_t j = lane; j < cn; j += 32) {
-      const M bj = sb[j];
 #pragma unroll
-      for (int r = 0; r < kGemvRowsPerWarp; ++r)
-        if (ok[r]) acc[r] += __ldg(a[r] + c0 + j) * bj;
+    for (int q = 0; q < NV; ++q) acc[r][q] = M(0);
+  }
+  for (int32_t c0 = 0; c0 < n; c0 += kChunk) {
+    const int32_t cn = min(kChunk, n - c0);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      for (int32_t j = threadIdx.x; j < cn; j += blockDim.x) sb[q][j] = (M)v.b[q][c0 + j];
+    __syncthreads();
+#pragma unroll 2
+    for (int32_t j = lane; j < cn; j += 32) {
+      M bj[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) bj[q] = sb[q][j];
+#pragma unroll
+      for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+        if (!ok[r]) continue;
+        const M av = __ldg(a[r] + c0 + j);
+#pragma unroll
+        for (int q = 0; q < NV; ++q) acc[r][q] += av * bj[q];
+      }
     }
   }
 #pragma unroll
   for (int r = 0; r < kGemvRowsPerWarp; ++r) {
-    M s = acc[r];
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (lane == 0 && ok[r]) x[row0 + r] = ADD ? x[row0 + r] + (T)s : (T)s;
+    for (int q = 0; q < NV; ++q) {
+      M s = acc[r][q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0 && ok[r]) v.x[q][row0 + r] = ADD ? v.x[q][row0 + r] + (T)s : (T)s;
+    }
   }
 }
 
 inline unsigned dense_gemv_blocks(int32_t n) {
   return (unsigned)((n + kGemvRowsPerBlock - 1) / kGemvRowsPerBlock);
+}
+
+// x_g (+)= A b_g for g < G, in launches of up to kGemvMaxVectors vectors.
+template <typename M, typename T, bool ADD>
+void launch_dense_gemv(const M* A, const T* const* b, T* const* x, int G, int32_t n,
+                       cudaStream_t st) {
+  for (int g0 = 0; g0 < G; g0 += kGemvMaxVectors) {
+    const int nv = G - g0 < kGemvMaxVectors ? G - g0 : kGemvMaxVectors;
+    GemvVectors<T> v{};
+    for (int q = 0; q < nv; ++q) {
+      v.b[q] = b[g0 + q];
+      v.x[q] = x[g0 + q];
+    }
+    const unsigned grid = dense_gemv_blocks(n);
+    switch (nv) {
+      case 1: k_dense_gemv<M, T, ADD, 1><<<grid, kGemvWarps * 32, 0, st>>>(A, v, n); break;
+      case 2: k_dense_gemv<M, T, ADD, 2><<<grid, kGemvWarps * 32, 0, st>>>(A, v, n); break;
+      case 3: k_dense_gemv<M, T, ADD, 3><<<grid, kGemvWarps * 32, 0, st>>>(A, v, n); break;
+      default: k_dense_gemv<M, T, ADD, 4><<<grid, kGemvWarps * 32, 0, st>>>(A, v, n); break;
+    }
+  }
 }
 
 }  // namespace cpm

@@ -283,71 +283,102 @@ static void transfer_residual(cpm_hier_s* H, Workspace& W, int l, const T* f, co
   }
 }
 
-// Coarsest level: explicit FP64 inverse, or weighted Jacobi sweeps from zero.
+// Systems that share one hierarchy and run one V-cycle in lockstep on one
+// stream: every step is issued for each member in turn (so each member's
+// arithmetic is exactly that of its own V-cycle), and the coarsest direct
+// solve reads the dense inverse once for all members.
+constexpr int kMaxGroup = 16;
+
+// Coarsest level: explicit FP64 or FP32 inverse, or weighted Jacobi sweeps from zero.
 template <typename T>
-static void coarse_solve(cpm_hier_s* H, Workspace& W, const T* f, T* u, cudaStream_t st) {
+static void coarse_solve(cpm_hier_s* H, Workspace* const* W, int G, const T* const* f, T* const* u,
+                         cudaStream_t st) {
   const int l = (int)H->L.size() - 1;
   if (H->coarse_mode == 0) {
-    launch_coarse_gemv<T>(H->Ainv.get(), f, u, H->nc, st);
+    launch_coarse_gemv<T>(H->Ainv.get(), f, u, G, H->nc, st);
     return;
   }
   if (H->coarse_mode == 1) {
-    launch_coarse_gemv32<T>(H->Ainv32.get(), f, u, H->nc, false, st);
+    launch_coarse_gemv32<T>(H->Ainv32.get(), f, u, G, H->nc, false, st);
     if constexpr (sizeof(T) == 8) {
       // two steps of iterative refinement with the FP64 residual of the level
       HLevel& lv = H->L[l];
       const LevelView<double> v = lv.view<double>();
+      const double* r[kMaxGroup];
+      for (int g = 0; g < G; ++g) r[g] = W[g]->w64[l].r.get();
       for (int it = 0; it < 2; ++it) {
-        launch_extend<double>(v, u, W.w64[l].w.get(), (int32_t)v.nplus, st);
-        launch_lap<double>(v, LAP_RESID, u, W.w64[l].w.get(), f, lv.c64.get(), H->c, nullptr, 0.0,
-                           W.w64[l].r.get(), nullptr, nullptr, 0, st);
-        launch_coarse_gemv32<double>(H->Ainv32.get(), W.w64[l].r.get(), u, H->nc, true, st);
+        for (int g = 0; g < G; ++g) {
+          Work<double>& w = W[g]->w64[l];
+          launch_extend<double>(v, u[g], w.w.get(), (int32_t)v.nplus, st);
+          launch_lap<double>(v, LAP_RESID, u[g], w.w.get(), f[g], lv.c64.get(), H->c, nullptr, 0.0,
+                             w.r.get(), nullptr, nullptr, 0, st);
+        }
+        launch_coarse_gemv32<double>(H->Ainv32.get(), r, u, G, H->nc, true, st);
       }
     }
     return;
   }
-  CPM_CUDA_TRY(cudaMemsetAsync(u, 0, sizeof(T) * H->L[l].lev->nB, st));
   HLevel& lv = H->L[l];
   const LevelView<T> v = lv.view<T>();
-  Work<T>& w = W.work<T>(l);
-  for (int s = 0; s < H->coarse_sweeps; ++s) {
-    launch_extend<T>(v, u, w.w.get(), (int32_t)v.nplus, st);
-    launch_lap<T>(v, LAP_JACOBI, u, w.w.get(), f, lv.cvec<T>(), (T)H->c, lv.dA<T>(),
-                  (T)H->opts.omega, nullptr, u, nullptr, 0, st);
+  for (int g = 0; g < G; ++g) {
+    CPM_CUDA_TRY(cudaMemsetAsync(u[g], 0, sizeof(T) * lv.lev->nB, st));
+    Work<T>& w = W[g]->work<T>(l);
+    for (int s = 0; s < H->coarse_sweeps; ++s) {
+      launch_extend<T>(v, u[g], w.w.get(), (int32_t)v.nplus, st);
+      launch_lap<T>(v, LAP_JACOBI, u[g], w.w.get(), f[g], lv.cvec<T>(), (T)H->c, lv.dA<T>(),
+                    (T)H->opts.omega, nullptr, u[g], nullptr, 0, st);
+    }
+  }
+}
+
+// V-cycle of Algorithm 4.1 from level l for G systems in lockstep.
+template <typename T>
+static void vcycle_level(cpm_hier_s* H, Workspace* const* W, int G, int l, const T* const* f,
+                         T* const* u, cudaStream_t st) {
+  const int nl = (int)H->L.size();
+  if (l == nl - 1) {
+    coarse_solve<T>(H, W, G, f, u, st);
+    return;
+  }
+  HLevel& lv = H->L[l];
+  HLevel& cv = H->L[l + 1];
+  const T* cf[kMaxGroup];
+  T* cu[kMaxGroup];
+  for (int g = 0; g < G; ++g) {
+    Work<T>& w = W[g]->work<T>(l);
+    Work<T>& cw = W[g]->work<T>(l + 1);
+    int pre = H->opts.nu1;
+    if constexpr (sizeof(T) == 4) {
+      if (l == 0 && H->learned_active && pre > 0) {
+        // learned smoother in place of the first Jacobi sweep: r = f - A u, u += net(r)
+        const LevelView<float> v = lv.view<float>();
+        launch_extend<float>(v, u[g], w.w.get(), (int32_t)v.nplus, st);
+        launch_lap<float>(v, LAP_RESID, u[g], w.w.get(), f[g], lv.cvec<float>(), (float)H->c, nullptr,
+                          0.f, w.r.get(), nullptr, nullptr, 0, st);
+        mlp_forward(H->mlp->params.get(), *H->mlpd, w.r.get(), 1.f / v.inv_h2, nullptr, u[g], nullptr,
+                    st);
+        --pre;
+      }
+    }
+    smooth<T>(H, *W[g], l, f[g], u[g], pre, st);
+    transfer_residual<T>(H, *W[g], l, f[g], u[g], w.r.get(), st);
+    launch_transfer<T>(tview<T>(lv.R, lv.lev->dim), w.r.get(), cw.f.get(), false, st);
+    if (l + 1 < nl - 1)
+      CPM_CUDA_TRY(cudaMemsetAsync(cw.u.get(), 0, sizeof(T) * cv.lev->nB, st));
+    cf[g] = cw.f.get();
+    cu[g] = cw.u.get();
+  }
+  vcycle_level<T>(H, W, G, l + 1, cf, cu, st);
+  for (int g = 0; g < G; ++g) {
+    launch_transfer<T>(tview<T>(lv.P, lv.lev->dim), cu[g], u[g], true, st);
+    smooth<T>(H, *W[g], l, f[g], u[g], H->opts.nu2, st);
   }
 }
 
 template <typename T>
 static void vcycle_level(cpm_hier_s* H, Workspace& W, int l, const T* f, T* u, cudaStream_t st) {
-  const int nl = (int)H->L.size();
-  if (l == nl - 1) {
-    coarse_solve<T>(H, W, f, u, st);
-    return;
-  }
-  HLevel& lv = H->L[l];
-  HLevel& cv = H->L[l + 1];
-  Work<T>& w = W.work<T>(l);
-  Work<T>& cw = W.work<T>(l + 1);
-  int pre = H->opts.nu1;
-  if constexpr (sizeof(T) == 4) {
-    if (l == 0 && H->learned_active && pre > 0) {
-      // learned smoother in place of the first Jacobi sweep: r = f - A u, u += net(r)
-      const LevelView<float> v = lv.view<float>();
-      launch_extend<float>(v, u, w.w.get(), (int32_t)v.nplus, st);
-      launch_lap<float>(v, LAP_RESID, u, w.w.get(), f, lv.cvec<float>(), (float)H->c, nullptr, 0.f,
-                        w.r.get(), nullptr, nullptr, 0, st);
-      mlp_forward(H->mlp->params.get(), *H->mlpd, w.r.get(), 1.f / v.inv_h2, nullptr, u, nullptr, st);
-      --pre;
-    }
-  }
-  smooth<T>(H, W, l, f, u, pre, st);
-  transfer_residual<T>(H, W, l, f, u, w.r.get(), st);
-  launch_transfer<T>(tview<T>(lv.R, lv.lev->dim), w.r.get(), cw.f.get(), false, st);
-  if (l + 1 < nl - 1)
-    CPM_CUDA_TRY(cudaMemsetAsync(cw.u.get(), 0, sizeof(T) * cv.lev->nB, st));
-  vcycle_level<T>(H, W, l + 1, cw.f.get(), cw.u.get(), st);
-  launch_transfer<T>(tview<T>(lv.P, lv.lev->dim), cw.u.get(), u, true, st);
-  smooth<T>(H, W, l, f, u, H->opts.nu2, st);
+  Workspace* w = &W;
+  vcycle_level<T>(H, &w, 1, l, &f, &u, st);
 }
 
 // FP64 outer residual r = f - A u on the finest level with norms into H->norms.
@@ -361,20 +392,40 @@ static void outer_residual(cpm_hier_s* H, Workspace& W, const double* f, const d
   launch_norm_final(W.part.get(), nblk(v.nB, 256), W.norms, st);
 }
 
-// One outer iteration after the residual: u += V(0, r), then the new residual.
-static void outer_step(cpm_hier_s* H, Workspace& W, int mode, int inner, cudaStream_t st) {
+// One outer iteration after the residual, for G systems of one hierarchy in
+// lockstep: u += V(0, r), then the new residual.
+static void outer_step(cpm_hier_s* H, Workspace* const* W, int G, int mode, int inner,
+                       cudaStream_t st) {
   const int64_t nB = H->L[0].lev->nB;
   if (mode == CPM_SOLVE_F64) {
-    CPM_CUDA_TRY(cudaMemsetAsync(W.d64.get(), 0, sizeof(double) * nB, st));
-    vcycle_level<double>(H, W, 0, W.r64.get(), W.d64.get(), st);
-    launch_axpy64(W.u_own.get(), W.d64.get(), nB, st);
+    const double* r[kMaxGroup];
+    double* d[kMaxGroup];
+    for (int g = 0; g < G; ++g) {
+      CPM_CUDA_TRY(cudaMemsetAsync(W[g]->d64.get(), 0, sizeof(double) * nB, st));
+      r[g] = W[g]->r64.get();
+      d[g] = W[g]->d64.get();
+    }
+    vcycle_level<double>(H, W, G, 0, r, d, st);
+    for (int g = 0; g < G; ++g) launch_axpy64(W[g]->u_own.get(), W[g]->d64.get(), nB, st);
   } else {
-    launch_scale_to_f32(W.r64.get(), W.norms, W.r32.get(), nB, st);
-    CPM_CUDA_TRY(cudaMemsetAsync(W.d32.get(), 0, sizeof(float) * nB, st));
-    for (int j = 0; j < inner; ++j) vcycle_level<float>(H, W, 0, W.r32.get(), W.d32.get(), st);
-    launch_axpy_scaled(W.u_own.get(), W.d32.get(), W.norms, nB, st);
+    const float* r[kMaxGroup];
+    float* d[kMaxGroup];
+    for (int g = 0; g < G; ++g) {
+      launch_scale_to_f32(W[g]->r64.get(), W[g]->norms, W[g]->r32.get(), nB, st);
+      CPM_CUDA_TRY(cudaMemsetAsync(W[g]->d32.get(), 0, sizeof(float) * nB, st));
+      r[g] = W[g]->r32.get();
+      d[g] = W[g]->d32.get();
+    }
+    for (int j = 0; j < inner; ++j) vcycle_level<float>(H, W, G, 0, r, d, st);
+    for (int g = 0; g < G; ++g) launch_axpy_scaled(W[g]->u_own.get(), W[g]->d32.get(), W[g]->norms, nB, st);
   }
-  outer_residual(H, W, W.f_own.get(), W.u_own.get(), W.r64.get(), st);
+  for (int g = 0; g < G; ++g)
+    outer_residual(H, *W[g], W[g]->f_own.get(), W[g]->u_own.get(), W[g]->r64.get(), st);
+}
+
+static void outer_step(cpm_hier_s* H, Workspace& W, int mode, int inner, cudaStream_t st) {
+  Workspace* w = &W;
+  outer_step(H, &w, 1, mode, inner, st);
 }
 
 }  // namespace cpm
@@ -1152,9 +1203,29 @@ static void cache_store(const cpm_batch_s& b, int k) {
   std::fclose(fp);
 }
 
-// Graph of one outer iteration of the systems in sys: K concurrent branches,
-// system sys[j] on branch j mod K.  Largest systems first so that the
-// branches finish close together.
+// Lockstep groups among the systems in sys: systems of one hierarchy, at
+// most kMaxGroup per group.
+static std::vector<std::vector<int>> make_groups(const cpm_batch_s& b, const std::vector<int>& sys) {
+  std::vector<std::vector<int>> groups;
+  std::vector<int> rest(sys);
+  while (!rest.empty()) {
+    std::vector<int> grp, other;
+    for (int s : rest)
+      (b.H[s] == b.H[rest[0]] && (int)grp.size() < kMaxGroup ? grp : other).push_back(s);
+    groups.push_back(grp);
+    rest.swap(other);
+  }
+  return groups;
+}
+
+static int count_groups(const cpm_batch_s& b, const std::vector<int>& sys) {
+  return (int)make_groups(b, sys).size();
+}
+
+// Graph of one outer iteration of the systems in sys on K concurrent
+// branches.  Systems of the same hierarchy form lockstep groups (up to
+// kMaxGroup, one coarse-inverse pass for all of them); groups go to branches
+// largest first, each to the branch with the least work so far.
 static void capture_batch(cpm_batch_s& b, const std::vector<int>& sys, int K, int mode, int inner) {
   if (b.graph && b.graph_k == K && b.graph_mode == mode && b.graph_inner == inner && b.graph_sys == sys)
     return;
@@ -1162,17 +1233,30 @@ static void capture_batch(cpm_batch_s& b, const std::vector<int>& sys, int K, in
     cudaGraphExecDestroy(b.graph);
     b.graph = nullptr;
   }
-  std::vector<int> order(sys);
-  std::stable_sort(order.begin(), order.end(),
-                   [&](int x, int y) { return b.H[x]->L[0].lev->nB > b.H[y]->L[0].lev->nB; });
+  std::vector<std::vector<int>> groups = make_groups(b, sys);
+  auto work = [&](const std::vector<int>& g) { return (double)b.H[g[0]]->L[0].lev->nB * g.size(); };
+  std::stable_sort(groups.begin(), groups.end(),
+                   [&](const std::vector<int>& x, const std::vector<int>& y) { return work(x) > work(y); });
+  std::vector<std::vector<int>> branch(K);  // group indices per branch
+  std::vector<double> load(K, 0.0);
+  for (size_t j = 0; j < groups.size(); ++j) {
+    const int k = (int)(std::min_element(load.begin(), load.end()) - load.begin());
+    branch[k].push_back((int)j);
+    load[k] += work(groups[j]);
+  }
   cudaGraph_t g;
   CPM_CUDA_TRY(cudaStreamBeginCapture(b.ms, cudaStreamCaptureModeThreadLocal));
   set_capturing(true);
   try {
     CPM_CUDA_TRY(cudaEventRecord(b.ev_fork, b.ms));
     for (int k = 0; k < K; ++k) CPM_CUDA_TRY(cudaStreamWaitEvent(b.fs[k], b.ev_fork, 0));
-    for (size_t j = 0; j < order.size(); ++j)
-      outer_step(b.H[order[j]], *b.W[order[j]], mode, inner, b.fs[j % K]);
+    for (int k = 0; k < K; ++k)
+      for (int j : branch[k]) {
+        Workspace* ws[kMaxGroup];
+        const std::vector<int>& g = groups[j];
+        for (size_t q = 0; q < g.size(); ++q) ws[q] = b.W[g[q]].get();
+        outer_step(b.H[g[0]], ws, (int)g.size(), mode, inner, b.fs[k]);
+      }
     for (int k = 0; k < K; ++k) {
       CPM_CUDA_TRY(cudaEventRecord(b.ev_join[k], b.fs[k]));
       CPM_CUDA_TRY(cudaStreamWaitEvent(b.ms, b.ev_join[k], 0));
@@ -1293,10 +1377,11 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
   }
   // autotuner: the first outer iterations try K = 1, 2, 4, ... concurrent
   // branches (each a real iteration of every active system)
-  std::vector<int> cand;
+  std::vector<int> cand, all_systems(ns);
+  for (int s = 0; s < ns; ++s) all_systems[s] = s;
   if (b->chosen == 0) b->chosen = cache_lookup(*b);
   if (b->chosen == 0)
-    for (int k = 1; k <= std::min(ns, kMaxBranches); k *= 2) cand.push_back(k);
+    for (int k = 1; k <= std::min(count_groups(*b, all_systems), kMaxBranches); k *= 2) cand.push_back(k);
   size_t ci = 0;
   double best_ms = 1e300;
   int best_k = b->chosen;
@@ -1331,7 +1416,7 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
     // over the active ones once they are at most half of it
     if (in_graph.empty() || 2 * active.size() <= in_graph.size()) in_graph = active;
     const int K = ci < cand.size() ? cand[ci] : (best_k > 0 ? best_k : 1);
-    capture_batch(*b, in_graph, std::min<int>(K, (int)in_graph.size()), o.mode, o.inner_cycles);
+    capture_batch(*b, in_graph, std::min<int>(K, count_groups(*b, in_graph)), o.mode, o.inner_cycles);
     CPM_CUDA_TRY(cudaEventRecord(b->t0, b->ms));
     CPM_CUDA_TRY(cudaGraphLaunch(b->graph, b->ms));
     CPM_CUDA_TRY(cudaEventRecord(b->t1, b->ms));

@@ -288,11 +288,12 @@ void launch_cast_from_f64(const double* x, T* y, int64_t n, cudaStream_t st) {
 }
 
 // ----------------------------------------------------------------- coarse solve
-// x = Ainv b with the FP64 inverse (chunked dense product, FP64 accumulation).
+// x_g = Ainv b_g with the FP64 inverse (chunked dense product, FP64 accumulation).
 template <typename T>
-void launch_coarse_gemv(const double* Ainv, const T* b, T* x, int32_t n, cudaStream_t st) {
-  k_dense_gemv<double, T, false><<<dense_gemv_blocks(n), kGemvWarps * 32, 0, st>>>(Ainv, b, x, n);
-  count_launch();
+void launch_coarse_gemv(const double* Ainv, const T* const* b, T* const* x, int G, int32_t n,
+                        cudaStream_t st) {
+  launch_dense_gemv<double, T, false>(Ainv, b, x, G, n, st);
+  count_launch((G + kGemvMaxVectors - 1) / kGemvMaxVectors);
 }
 
 // ----------------------------------------------------------------- setup: diag(M)
@@ -487,7 +488,8 @@ void invert_dense(double* A, int32_t n, cudaStream_t st, int32_t* err) {
   template void launch_norm_partials<T>(const T*, int64_t, double*, cudaStream_t);               \
   template void launch_cast_to_f64<T>(const T*, double*, int64_t, cudaStream_t);                 \
   template void launch_cast_from_f64<T>(const double*, T*, int64_t, cudaStream_t);               \
-  template void launch_coarse_gemv<T>(const double*, const T*, T*, int32_t, cudaStream_t);
+  template void launch_coarse_gemv<T>(const double*, const T* const*, T* const*, int, int32_t, \
+                                      cudaStream_t);
 CPM_INST(double)
 CPM_INST(float)
 

@@ -87,18 +87,20 @@ void launch_cast_to_f64(const T* x, double* y, int64_t n, cudaStream_t st);
 template <typename T>
 void launch_cast_from_f64(const double* x, T* y, int64_t n, cudaStream_t st);
 
-// Coarsest direct solve x = Ainv b (FP64 matrix, FP64 accumulation).
+// Coarsest direct solve x_g = Ainv b_g, g < G (FP64 matrix, FP64 accumulation).
 template <typename T>
-void launch_coarse_gemv(const double* Ainv, const T* b, T* x, int32_t n, cudaStream_t st);
+void launch_coarse_gemv(const double* Ainv, const T* const* b, T* const* x, int G, int32_t n,
+                        cudaStream_t st);
 
 // Residual norms of the finest level with the library's fixed device scratch
 // (noalloc.cu); norms[0] = max|r|, norms[1] = sum r^2 (device).
 void residual_norms_noalloc(const LevelView<double>& v, const double* f, const double* u,
                             const double* cvec, double cval, double* norms, cudaStream_t st);
 
-// Coarsest solve with an FP32 explicit inverse (coarse32.cu): x (+)= Ainv b.
+// Coarsest solve with an FP32 explicit inverse (coarse32.cu): x_g (+)= Ainv b_g.
 template <typename T>
-void launch_coarse_gemv32(const float* Ainv, const T* b, T* x, int32_t n, bool add, cudaStream_t st);
+void launch_coarse_gemv32(const float* Ainv, const T* const* b, T* const* x, int G, int32_t n, bool add,
+                          cudaStream_t st);
 // A (row-major FP32, overwritten) -> X = A^-1 (library LU, setup only).
 void invert_dense_f32(float* A, float* X, int32_t n, cudaStream_t st, int32_t* err);
 
