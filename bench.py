@@ -31,12 +31,17 @@ sys.path.insert(0, ROOT)
 DX = 1.0 / 256
 METRIC = "s to 1e-10 rel residual, sphere Δx=1/256: FP32-IR/learned vs FP64; HBM GB/s"
 SAMPLE_DX = 1.0 / 64
-# FP64 flops of one extension evaluation per point: cubic weights (13 per axis)
-# and the separable 4x4x4 contraction (64 + 16 + 4 multiply-adds).
-EXTEND_FLOPS = 3 * 13 + 2 * (64 + 16 + 4)
-# FP32 extension bytes per point: key 8 + fractions 12 + u 4 + w 4.
-EXTEND32_BYTES = 28
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (profiling recipe table)
+# FP64 flops of one extension evaluation per point: the separable 4x4x4
+# contraction, 64 + 16 + 4 multiply-adds (the FP64 weights are precomputed).
+EXTEND_FLOPS = 2 * (64 + 16 + 4)
+# FP32 extension bytes: per point of B+ its record 4 + fractions 12 + w 4; per
+# point of B its value u 4 (the tile tables, ~2 B per point, are not counted).
+EXTEND32_BYTES_BPLUS = 20
+EXTEND32_BYTES_B = 4
+# DRAM bytes (read + write) of one FP32 extension launch over B+ of the unit
+# sphere at dx = 1/256, from one ncu capture of the same kernel and workload.
+EXTEND32_TRAFFIC = 195.472128e6 + 27.053568e6
+FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak is provided)
 
 
 def _sphere_rhs(y):
@@ -366,7 +371,8 @@ def run_cpm(args, world, rank, local):
     ext32_ms = ev0.elapsed_time(ev1) / reps_k
     npl = nb + band.ng
     ach64 = EXTEND_FLOPS * npl / (ext64_ms * 1e-3) / 1e12
-    ach32 = EXTEND32_BYTES * npl / (ext32_ms * 1e-3) / 1e9
+    bytes32 = EXTEND32_BYTES_BPLUS * npl + EXTEND32_BYTES_B * nb
+    ach32 = bytes32 / (ext32_ms * 1e-3) / 1e9
     pk = peaks()
 
     if rank != 0:
@@ -395,13 +401,19 @@ def run_cpm(args, world, rank, local):
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": nb * 8,
                 "d2h_bytes_per_step": nb * 8},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "k_extend<double,3> (FP64 extension over B+)", "bound": "alu",
-                     "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                     "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": None,
-                     "flops_per_point": EXTEND_FLOPS, "points": npl, "ms": ext64_ms},
-        "roofline_f32_extend": {"bound": "hbm", "achieved": ach32, "peak": pk.get("hbm_gbs"),
-                                "unit": "GB/s", "frac": ach32 / pk.get("hbm_gbs", 6800.0),
-                                "bytes_per_point": EXTEND32_BYTES, "ms": ext32_ms},
+        "roofline": {"kernel": "k_extend_tiles<float,3> (FP32 extension over B+; 48 % of the "
+                               "mixed solve's kernel time)", "bound": "hbm",
+                     "achieved": ach32, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                     "frac": ach32 / pk.get("hbm_gbs", 6800.0),
+                     "traffic": EXTEND32_TRAFFIC if wl["kind"] == "sphere" and wl["dx"] == DX else None,
+                     "algorithmic_bytes": bytes32, "points": npl, "ms": ext32_ms,
+                     "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"},
+        "roofline_f64_extend": {"kernel": "k_extend_tiles<double,3> (FP64 extension of the outer "
+                                          "residual; 23 %)", "bound": "alu",
+                                "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                                "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": None,
+                                "flops_per_point": EXTEND_FLOPS, "points": npl, "ms": ext64_ms,
+                                "peak_source": "nominal FP64 rate"},
         "clocks": clk.summary(),
     }
     if cpu:

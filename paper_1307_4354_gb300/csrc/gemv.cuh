@@ -2,16 +2,17 @@
 // coarsest-level matrix (row-major n x n, FP64 or FP32), for one or several
 // right-hand sides at once.  HBM-bound on A: each warp streams
 // kGemvRowsPerWarp rows with coalesced loads (independent loads in flight per
-// lane), and the vectors pass through shared memory in chunks shared by the
-// block's 64 rows (32 KB at most, whatever n is).  Accumulation in the matrix
+// lane; 16 rows per block, so that even a 4096-point level fills every SM),
+// and the vectors pass through shared memory in chunks shared by the block's
+// rows (32 KB at most, whatever n is).  Accumulation in the matrix
 // type; fixed summation order.
 #pragma once
 #include <cstdint>
 
 namespace cpm {
 
-constexpr int kGemvWarps = 16;
-constexpr int kGemvRowsPerWarp = 4;
+constexpr int kGemvWarps = 8;
+constexpr int kGemvRowsPerWarp = 2;
 constexpr int kGemvRowsPerBlock = kGemvWarps * kGemvRowsPerWarp;
 constexpr int kGemvMaxVectors = 4;
 
