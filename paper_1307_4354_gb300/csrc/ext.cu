@@ -239,6 +239,14 @@ __device__ __forceinline__ void load4(const double* p, double v[4]) {
   v[0] = a.x; v[1] = a.y; v[2] = b.x; v[3] = b.y;
 }
 
+__device__ __forceinline__ void store4(float* p, float a, float b, float c, float d) {
+  *reinterpret_cast<float4*>(p) = make_float4(a, b, c, d);
+}
+__device__ __forceinline__ void store4(double* p, double a, double b, double c, double d) {
+  *reinterpret_cast<double2*>(p) = make_double2(a, b);
+  *reinterpret_cast<double2*>(p + 2) = make_double2(c, d);
+}
+
 constexpr int kExtThreads = 64;
 
 template <typename T>
@@ -316,43 +324,40 @@ __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, co
   }
   __syncthreads();
   // stage the nodes the tile's stencils read: bases span [lo, hi] per axis,
-  // so box nodes lo .. hi+3.  Thread (x, y) walks z; node x feeds windows
-  // x0 = max(lo_x, x-3) .. min(hi_x, x), at offset 3*x0 + x in its row.
+  // so box nodes lo .. hi+3.  Thread r owns box row (y, z): it reads the
+  // row's band nodes in order (consecutive band indices within each of the
+  // row's two bricks, so one popcount per brick gives the start) and writes
+  // the row's windows x0 = lo_x .. hi_x, four values each, as vector stores.
   {
     const int xlo = tbox & 3, xhi = (tbox >> 2) & 3;
     const int ylo = (tbox >> 4) & 3, yhi = (tbox >> 6) & 3;
     const int zlo = DIM == 3 ? (tbox >> 8) & 3 : 0, zhi = DIM == 3 ? ((tbox >> 10) & 3) + 3 : 0;
-    const int x = xlo + (threadIdx.x & 7), y = ylo + (threadIdx.x >> 3);
-    if (x <= xhi + 3 && y <= yhi + 3) {
-      const int jxy = (x >> 2) | ((y >> 2) << 1);
-      const uint32_t lbit = 1u << ((x & 3) | ((y & 3) << 2));
-      const int x0a = max(xlo, x - 3), x0b = min(xhi, x);
-      const bool p0 = x0a <= 0 && 0 <= x0b, p1 = x0a <= 1 && 1 <= x0b;
-      const bool p2 = x0a <= 2 && 2 <= x0b, p3 = x0a <= 3 && 3 <= x0b;
-      // all loads of the column first, then the shared-memory stores
-      T v[NZ];
+    const int ny = yhi + 4 - ylo;
+    const int r = threadIdx.x;
+    if (r < ny * (zhi + 1 - zlo)) {
+      const int y = ylo + r % ny, z = zlo + r / ny;
+      const int jyz = ((y >> 2) << 1) | ((z >> 2) << 2);
+      const int half = (z >> 1) & 1;
+      const int shift = ((y & 3) << 2) | ((z & 1) << 4);
+      const uint32_t wa = sm_mask[jyz][half], wb = sm_mask[jyz | 1][half];
+      const uint32_t rba = (wa >> shift) & 0xFu, rbb = (wb >> shift) & 0xFu;
+      const uint32_t below = (1u << shift) - 1u;
+      int32_t ca = sm_start[jyz][half] + __popc(wa & below) + __popc(rba & ((1u << xlo) - 1u));
+      int32_t cb = sm_start[jyz | 1][half] + __popc(wb & below);
+      T v[7];
 #pragma unroll
-      for (int dz = 0; dz < NZ; ++dz) {
-        const int z = zlo + dz;
-        v[dz] = T(0);
-        if (z <= zhi) {
-          const int j = jxy | ((z >> 2) << 2);
-          const int half = (z >> 1) & 1;
-          const uint32_t m = sm_mask[j][half];
-          const uint32_t bit = lbit << ((z & 1) << 4);
-          if (m & bit) v[dz] = __ldg(u + sm_start[j][half] + __popc(m & (bit - 1)));
+      for (int i = 0; i < 7; ++i) {
+        const int x = xlo + i;
+        v[i] = T(0);
+        if (x <= xhi + 3) {
+          const bool hi = x >= 4;
+          if (((hi ? rbb : rba) >> (x & 3)) & 1u) v[i] = __ldg(u + (hi ? cb++ : ca++));
         }
       }
-      T* row = win + (zlo * 7 + y) * RS + x;
+      T* row = win + (z * 7 + y) * RS;
 #pragma unroll
-      for (int dz = 0; dz < NZ; ++dz, row += 7 * RS) {
-        if (zlo + dz <= zhi) {
-          if (p0) row[0] = v[dz];
-          if (p1) row[3] = v[dz];
-          if (p2) row[6] = v[dz];
-          if (p3) row[9] = v[dz];
-        }
-      }
+      for (int i = 0; i < 4; ++i)
+        if (xlo + i <= xhi) store4(row + 4 * (xlo + i), v[i], v[i + 1], v[i + 2], v[i + 3]);
     }
   }
   __syncthreads();
