@@ -152,14 +152,15 @@ struct Level {
   DBuf<double> cp;    // d x (nB+nG), SoA
   DBuf<double> fr64;  // d x (nB+nG), SoA
   DBuf<float> fr32;   // d x (nB+nG), SoA
-  // extension tiles: the points of B (then of G) grouped by the brick that
-  // holds their cubic stencil base ("E order"); see ext.cu
-  int32_t ntiles_B = 0, ntiles = 0;
+  // extension tiles: the points of B+ grouped by the brick that holds their
+  // cubic stencil base, points of B first in each tile ("E order"); see ext.cu
+  int32_t ntiles = 0;
   DBuf<uint32_t> tile_brick;  // packed brick coordinates of each tile
   DBuf<uint32_t> tile_box;    // per axis: lowest and highest base position in the brick
   DBuf<uint64_t> tile_mask;   // 8 per tile: band masks of the bricks the tile's box overlaps
   DBuf<int32_t> tile_bstart;  // 8 per tile: their band starts
   DBuf<int32_t> tile_start;   // ntiles + 1 offsets into the E-order arrays
+  DBuf<int32_t> tile_mid;     // per tile: end of its points of B
   DBuf<uint32_t> erec;        // band index << 6 | stencil base inside the brick
   DBuf<float> efr32;          // d x (nB+nG) fractions in E order
   DBuf<double> ew64;          // 4d x (nB+nG) FP64 cubic weights in E order

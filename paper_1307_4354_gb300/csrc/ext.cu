@@ -2,8 +2,9 @@
 // Eq. 4.2b): w_i = sum over the 4^d stencil nodes of cp(x_i) of the tensor
 // product of 1-D cubic Lagrange weights times u.
 //
-// Tiling.  The points of B (then, separately, of the ghost ring G) are grouped
-// by the 4^d brick that holds their stencil base node.  A tile's stencils all
+// Tiling.  The points of B+ are grouped by the 4^d brick that holds their
+// stencil base node, the points of B first in each tile (an extension over B
+// alone stops at the tile's last point of B).  A tile's stencils all
 // lie in the fixed 7^d box starting at the brick's first node, so one CTA
 // stages that box from HBM/L2 into shared memory once (with the brick map and
 // occupancy masks) and evaluates every point of the tile from it.  Each box
@@ -19,8 +20,8 @@ namespace cpm {
 static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // ----------------------------------------------------------------- tile build
-__global__ void k_tile_slots(BrickView v, const uint64_t* key, int64_t nplus, int32_t nB,
-                             int32_t nbricks, int dim, int32_t* slot, int64_t* count, int32_t* err,
+__global__ void k_tile_slots(BrickView v, const uint64_t* key, int64_t nplus, int32_t nB, int dim,
+                             int32_t* slot, int64_t* count, int64_t* count_B, int32_t* err,
                              int32_t* bbox) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nplus) return;
@@ -35,9 +36,10 @@ __global__ void k_tile_slots(BrickView v, const uint64_t* key, int64_t nplus, in
     slot[i] = -1;
     return;
   }
-  const int32_t s = (i < nB ? 0 : nbricks) + b;
+  const int32_t s = b;
   slot[i] = s;
   atomicAdd(reinterpret_cast<unsigned long long*>(count + s), 1ull);
+  if (i < nB) atomicAdd(reinterpret_cast<unsigned long long*>(count_B + s), 1ull);
   // bounding box of the stencil bases inside the brick: bits (min, max) per axis
   const int l[3] = {bx & 3, by & 3, bz & 3};
   int32_t bits = 0;
@@ -50,14 +52,16 @@ __global__ void k_tile_flags(const int64_t* count, int64_t n, int64_t* flag) {
   if (i < n) flag[i] = count[i] > 0;
 }
 
-__global__ void k_tile_emit(const int64_t* count, const int64_t* offset, const int64_t* tpos,
-                            const uint32_t* bcoord, const int32_t* bbox, int64_t n, int32_t nbricks,
-                            uint32_t* tile_brick, uint32_t* tile_box, int32_t* tile_start) {
+__global__ void k_tile_emit(const int64_t* count, const int64_t* count_B, const int64_t* offset,
+                            const int64_t* tpos, const uint32_t* bcoord, const int32_t* bbox,
+                            int64_t n, uint32_t* tile_brick, uint32_t* tile_box, int32_t* tile_start,
+                            int32_t* tile_mid) {
   const int64_t s = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (s >= n || count[s] == 0) return;
   const int64_t t = tpos[s];
-  tile_brick[t] = bcoord[s % nbricks];
+  tile_brick[t] = bcoord[s];
   tile_start[t] = (int32_t)offset[s];
+  tile_mid[t] = (int32_t)(offset[s] + count_B[s]);
   // packed per axis: lowest and highest base position used (2 bits each)
   uint32_t packed = 0;
   for (int a = 0; a < 3; ++a) {
@@ -121,31 +125,32 @@ __global__ void k_tile_tables(BrickView v, const uint32_t* tile_brick, int32_t n
   tstart[q] = s0;
 }
 
-// Order the points of each tile by (stencil base position, band index): points
-// with equal bases become neighbours in a warp (shared-memory broadcasts instead
-// of bank conflicts) and the E order no longer depends on atomics.  Tiles of
-// more than kSortMax points keep their order.
-constexpr int kSortMax = 4096;
-__global__ void k_tile_sort(const int32_t* tile_start, int64_t nplus, int dim, const uint32_t* erec,
-                            const float* efr32, const double* ew64, uint32_t* erec2, float* efr2,
-                            double* ew2) {
-  __shared__ uint32_t keys[kSortMax];
+// Order the points of each tile by (point of G, stencil base position, band
+// index): the points of B come first, points with equal bases become
+// neighbours in a warp (shared-memory broadcasts instead of bank conflicts),
+// and the E order no longer depends on atomics.  The keys are distinct (band
+// indices are), so the ranks are a permutation.  Tiles of more than kSortMax
+// points rank from global memory.
+constexpr int kSortMax = 2048;
+__device__ __forceinline__ uint64_t tile_sort_key(uint32_t r, int32_t nB) {
+  const uint32_t idx = r >> 6;
+  return ((uint64_t)(idx >= (uint32_t)nB) << 32) | ((uint64_t)(r & 63u) << 26) | idx;
+}
+__global__ void k_tile_sort(const int32_t* tile_start, int64_t nplus, int32_t nB, int dim,
+                            const uint32_t* erec, const float* efr32, const double* ew64,
+                            uint32_t* erec2, float* efr2, double* ew2) {
+  __shared__ uint64_t keys[kSortMax];
   const int32_t beg = tile_start[blockIdx.x], end = tile_start[blockIdx.x + 1];
   const int n = end - beg;
-  const bool sort = n <= kSortMax;
-  if (sort)
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const uint32_t r = erec[beg + j];
-      keys[j] = ((r & 63u) << 26) | (r >> 6);
-    }
+  const bool in_smem = n <= kSortMax;
+  if (in_smem)
+    for (int j = threadIdx.x; j < n; j += blockDim.x) keys[j] = tile_sort_key(erec[beg + j], nB);
   __syncthreads();
   for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    int rank = j;
-    if (sort) {
-      const uint32_t kj = keys[j];
-      rank = 0;
-      for (int i = 0; i < n; ++i) rank += keys[i] < kj;
-    }
+    const uint64_t kj = in_smem ? keys[j] : tile_sort_key(erec[beg + j], nB);
+    int rank = 0;
+    for (int i = 0; i < n; ++i)
+      rank += (in_smem ? keys[i] : tile_sort_key(erec[beg + i], nB)) < kj;
     const int64_t src = beg + j, dst = beg + rank;
     erec2[dst] = erec[src];
     for (int a = 0; a < dim; ++a) efr2[a * nplus + dst] = efr32[a * nplus + src];
@@ -156,42 +161,32 @@ __global__ void k_tile_sort(const int32_t* tile_start, int64_t nplus, int dim, c
 void build_ext_tiles(Level& L, cudaStream_t st) {
   const int64_t np = L.nplus();
   CPM_CHECK(np < (1ll << 26), CPM_ERR_ARG, "more than 2^26 points on one level");
-  const int64_t nslots = 2 * (int64_t)L.nbricks;
+  const int64_t nslots = (int64_t)L.nbricks;
   DBuf<int32_t> slot(np);
-  DBuf<int64_t> count(nslots), offset(nslots), cursor(nslots), tpos(nslots);
+  DBuf<int64_t> count(nslots), count_B(nslots), offset(nslots), cursor(nslots), tpos(nslots);
   DBuf<int32_t> err(1), bbox(nslots);
   CPM_CUDA_TRY(cudaMemsetAsync(bbox.get(), 0, nslots * sizeof(int32_t), st));
   CPM_CUDA_TRY(cudaMemsetAsync(count.get(), 0, nslots * sizeof(int64_t), st));
+  CPM_CUDA_TRY(cudaMemsetAsync(count_B.get(), 0, nslots * sizeof(int64_t), st));
   CPM_CUDA_TRY(cudaMemsetAsync(cursor.get(), 0, nslots * sizeof(int64_t), st));
   CPM_CUDA_TRY(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), st));
-  k_tile_slots<<<nblk(np, 256), 256, 0, st>>>(L.view(), L.key.get(), np, L.nB, L.nbricks, L.dim,
-                                              slot.get(), count.get(), err.get(), bbox.get());
+  k_tile_slots<<<nblk(np, 256), 256, 0, st>>>(L.view(), L.key.get(), np, L.nB, L.dim, slot.get(),
+                                              count.get(), count_B.get(), err.get(), bbox.get());
   CPM_CUDA_TRY(cudaGetLastError());
   CPM_CUDA_TRY(cudaMemcpyAsync(offset.get(), count.get(), nslots * sizeof(int64_t),
                                cudaMemcpyDeviceToDevice, st));
   scan_exclusive_i64(offset.get(), nslots, st);
   k_tile_flags<<<nblk(nslots, 256), 256, 0, st>>>(count.get(), nslots, tpos.get());
   const int64_t ntiles = scan_exclusive_i64(tpos.get(), nslots, st);
-  // tiles of B come first (slots < nbricks)
-  int64_t ntB = 0;
-  if (L.nbricks > 0) {
-    int64_t last_pos = 0, last_cnt = 0;
-    CPM_CUDA_TRY(cudaMemcpyAsync(&last_pos, tpos.get() + L.nbricks - 1, sizeof(int64_t),
-                                 cudaMemcpyDeviceToHost, st));
-    CPM_CUDA_TRY(cudaMemcpyAsync(&last_cnt, count.get() + L.nbricks - 1, sizeof(int64_t),
-                                 cudaMemcpyDeviceToHost, st));
-    CPM_CUDA_TRY(cudaStreamSynchronize(st));
-    ntB = last_pos + (last_cnt > 0);
-  }
   L.ntiles = (int32_t)ntiles;
-  L.ntiles_B = (int32_t)ntB;
   L.tile_brick.alloc(ntiles);
   L.tile_box.alloc(ntiles);
   L.tile_start.alloc(ntiles + 1);
-  k_tile_emit<<<nblk(nslots, 256), 256, 0, st>>>(count.get(), offset.get(), tpos.get(),
-                                                 L.bcoord.get(), bbox.get(), nslots, L.nbricks,
+  L.tile_mid.alloc(ntiles);
+  k_tile_emit<<<nblk(nslots, 256), 256, 0, st>>>(count.get(), count_B.get(), offset.get(), tpos.get(),
+                                                 L.bcoord.get(), bbox.get(), nslots,
                                                  L.tile_brick.get(), L.tile_box.get(),
-                                                 L.tile_start.get());
+                                                 L.tile_start.get(), L.tile_mid.get());
   const int32_t npi = (int32_t)np;
   CPM_CUDA_TRY(cudaMemcpyAsync(L.tile_start.get() + ntiles, &npi, sizeof(int32_t),
                                cudaMemcpyHostToDevice, st));
@@ -212,9 +207,9 @@ void build_ext_tiles(Level& L, cudaStream_t st) {
     DBuf<float> efr2((size_t)L.dim * np);
     DBuf<double> ew2((size_t)4 * L.dim * np);
     if (ntiles > 0)
-      k_tile_sort<<<(unsigned)ntiles, 256, 0, st>>>(L.tile_start.get(), np, L.dim, L.erec.get(),
-                                                    L.efr32.get(), L.ew64.get(), erec2.get(),
-                                                    efr2.get(), ew2.get());
+      k_tile_sort<<<(unsigned)ntiles, 256, 0, st>>>(L.tile_start.get(), np, L.nB, L.dim,
+                                                    L.erec.get(), L.efr32.get(), L.ew64.get(),
+                                                    erec2.get(), efr2.get(), ew2.get());
     CPM_CUDA_TRY(cudaGetLastError());
     CPM_CUDA_TRY(cudaStreamSynchronize(st));
     L.erec = std::move(erec2);
@@ -294,7 +289,7 @@ struct PointWeights<float, DIM> {
 // values plus one pad window (row stride 20 values spreads rows over banks).
 template <typename T, int DIM>
 __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, const T* __restrict__ u,
-                                                              T* __restrict__ w) {
+                                                              T* __restrict__ w, bool with_ghost) {
   constexpr int NZ = DIM == 3 ? 7 : 1;
   constexpr int RS = 20;
   constexpr int NB = DIM == 3 ? 8 : 4;  // bricks overlapping the box
@@ -303,7 +298,9 @@ __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, co
   __shared__ int32_t sm_start[NB][2];
   const int32_t tile = blockIdx.x;
   const uint32_t tbox = __ldg(L.tile_box + tile);
-  const int32_t beg = __ldg(L.tile_start + tile), end = __ldg(L.tile_start + tile + 1);
+  const int32_t beg = __ldg(L.tile_start + tile);
+  const int32_t end = with_ghost ? __ldg(L.tile_start + tile + 1) : __ldg(L.tile_mid + tile);
+  if (beg == end) return;  // a tile of ghost points only, extension over B
   // this thread's first point: issue its record loads before staging
   int32_t k = beg + threadIdx.x;
   uint32_t rec = 0;
@@ -387,12 +384,13 @@ __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, co
 template <typename T>
 void launch_extend(const LevelView<T>& L, const T* u, T* w, int32_t npts, cudaStream_t st) {
   if (npts <= 0) return;
-  const int32_t nt = npts > L.nB ? L.ntiles : L.ntiles_B;
+  const int32_t nt = L.ntiles;
   if (nt <= 0) return;
+  const bool with_ghost = npts > L.nB;
   if (L.dim == 3)
-    k_extend_tiles<T, 3><<<nt, kExtThreads, 0, st>>>(L, u, w);
+    k_extend_tiles<T, 3><<<nt, kExtThreads, 0, st>>>(L, u, w, with_ghost);
   else
-    k_extend_tiles<T, 2><<<nt, kExtThreads, 0, st>>>(L, u, w);
+    k_extend_tiles<T, 2><<<nt, kExtThreads, 0, st>>>(L, u, w, with_ghost);
   count_launch();
 }
 

@@ -109,10 +109,10 @@ LevelView<double> HLevel::view<double>() const {
   v.tile_mask = lev->tile_mask.get();
   v.tile_bstart = lev->tile_bstart.get();
   v.tile_start = lev->tile_start.get();
+  v.tile_mid = lev->tile_mid.get();
   v.erec = lev->erec.get();
   v.efr = lev->efr32.get();
   v.ew64 = lev->ew64.get();
-  v.ntiles_B = lev->ntiles_B;
   v.ntiles = lev->ntiles;
   v.nbr = lev->nbr.get();
   return v;
@@ -133,10 +133,10 @@ LevelView<float> HLevel::view<float>() const {
   v.tile_mask = lev->tile_mask.get();
   v.tile_bstart = lev->tile_bstart.get();
   v.tile_start = lev->tile_start.get();
+  v.tile_mid = lev->tile_mid.get();
   v.erec = lev->erec.get();
   v.efr = lev->efr32.get();
   v.ew64 = lev->ew64.get();
-  v.ntiles_B = lev->ntiles_B;
   v.ntiles = lev->ntiles;
   v.nbr = lev->nbr.get();
   return v;
@@ -560,8 +560,8 @@ static void copy_level(const Level& a, Level& b, cudaStream_t st) {
   cp(b.map, a.map); cp(b.bmask, a.bmask); cp(b.gmask, a.gmask); cp(b.bstart, a.bstart);
   cp(b.gstart, a.gstart); cp(b.bcoord, a.bcoord); cp(b.key, a.key); cp(b.cp, a.cp);
   cp(b.fr64, a.fr64); cp(b.fr32, a.fr32);
-  b.ntiles_B = a.ntiles_B; b.ntiles = a.ntiles;
-  cp(b.tile_brick, a.tile_brick); cp(b.tile_box, a.tile_box); cp(b.tile_mask, a.tile_mask); cp(b.tile_bstart, a.tile_bstart); cp(b.tile_start, a.tile_start); cp(b.erec, a.erec);
+  b.ntiles = a.ntiles;
+  cp(b.tile_brick, a.tile_brick); cp(b.tile_box, a.tile_box); cp(b.tile_mask, a.tile_mask); cp(b.tile_bstart, a.tile_bstart); cp(b.tile_start, a.tile_start); cp(b.tile_mid, a.tile_mid); cp(b.erec, a.erec);
   cp(b.efr32, a.efr32); cp(b.ew64, a.ew64); cp(b.nbr, a.nbr);
 }
 

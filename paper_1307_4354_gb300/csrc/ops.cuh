@@ -23,10 +23,11 @@ struct LevelView {
   const uint64_t* tile_mask;
   const int32_t* tile_bstart;
   const int32_t* tile_start;
+  const int32_t* tile_mid;  // per tile: end of its points of B
   const uint32_t* erec;
   const float* efr;     // E-order FP32 fractions
   const double* ew64;   // E-order FP64 weights
-  int32_t ntiles_B, ntiles;
+  int32_t ntiles;
   const int32_t* nbr;   // 2d x nB neighbour indices into B+
 };
 
