@@ -285,6 +285,62 @@ struct PointWeights<float, DIM> {
   }
 };
 
+// The separable contraction of one point's 4^d stencil read from the windows
+// at base (row stride 20 values, plane stride 7 rows).  FP64: x, then y, then
+// z.  FP32: y and z first with paired FMAs (two x positions per instruction,
+// Blackwell's packed FP32 FMA), then x: 32 + 8 + 2 packed operations instead
+// of 84 scalar ones.
+template <int DIM>
+__device__ __forceinline__ double contract(const double* base, const PointWeights<double, DIM>& pw) {
+  constexpr int RS = 20;
+  double acc = 0.0;
+#pragma unroll
+  for (int c = 0; c < (DIM == 3 ? 4 : 1); ++c) {
+    double accy = 0.0;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      double vv[4];
+      load4(base + (c * 7 + b) * RS, vv);
+      accy += pw.wy[b] * dot4(pw.wx, vv);
+    }
+    acc += (DIM == 3 ? pw.wz[c] : 1.0) * accy;
+  }
+  return acc;
+}
+template <int DIM>
+__device__ __forceinline__ float contract(const float* base, const PointWeights<float, DIM>& pw) {
+  constexpr int RS = 20;
+  float2 q01 = make_float2(0.f, 0.f), q23 = q01;
+#pragma unroll
+  for (int c = 0; c < (DIM == 3 ? 4 : 1); ++c) {
+    float2 p01, p23;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const float4 v = *reinterpret_cast<const float4*>(base + (c * 7 + b) * RS);
+      const float2 wyb = make_float2(pw.wy[b], pw.wy[b]);
+      if (b == 0) {
+        p01 = __fmul2_rn(wyb, make_float2(v.x, v.y));
+        p23 = __fmul2_rn(wyb, make_float2(v.z, v.w));
+      } else {
+        p01 = __ffma2_rn(wyb, make_float2(v.x, v.y), p01);
+        p23 = __ffma2_rn(wyb, make_float2(v.z, v.w), p23);
+      }
+    }
+    const float wzc = DIM == 3 ? pw.wz[c] : 1.f;
+    const float2 wz2 = make_float2(wzc, wzc);
+    if (c == 0) {
+      q01 = __fmul2_rn(wz2, p01);
+      q23 = __fmul2_rn(wz2, p23);
+    } else {
+      q01 = __ffma2_rn(wz2, p01, q01);
+      q23 = __ffma2_rn(wz2, p23, q23);
+    }
+  }
+  const float2 t = __ffma2_rn(make_float2(pw.wx[2], pw.wx[3]), q23,
+                              __fmul2_rn(make_float2(pw.wx[0], pw.wx[1]), q01));
+  return t.x + t.y;
+}
+
 // One CTA per tile.  Shared memory: NZ*7 box rows, each 4 windows of 4
 // values plus one pad window (row stride 20 values spreads rows over banks).
 template <typename T, int DIM>
@@ -360,19 +416,7 @@ __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, co
   __syncthreads();
   for (; k < end; k += kExtThreads) {
     const T* base = win + ((rec >> 4) & 3) * 7 * RS + ((rec >> 2) & 3) * RS + (rec & 3) * 4;
-    T acc = T(0);
-#pragma unroll
-    for (int c = 0; c < (DIM == 3 ? 4 : 1); ++c) {
-      T accy = T(0);
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        T vv[4];
-        load4(base + (c * 7 + b) * RS, vv);
-        accy += pw.wy[b] * dot4(pw.wx, vv);
-      }
-      acc += (DIM == 3 ? pw.wz[c] : T(1)) * accy;
-    }
-    w[rec >> 6] = acc;
+    w[rec >> 6] = contract<DIM>(base, pw);
     const int32_t kn = k + kExtThreads;
     if (kn < end) {
       rec = __ldg(L.erec + kn);
