@@ -566,7 +566,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="cpm", choices=["cpm", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--inner", type=int, default=2, help="FP32 V-cycles per outer iteration")
+    ap.add_argument("--inner", type=int, default=3, help="FP32 V-cycles per outer iteration")
     ap.add_argument("--residual", default="plain", choices=["extended", "plain"],
                     help="residual restricted in the V-cycle: f - A(E u) (Sec. 4.4) or f - A u")
     ap.add_argument("--nu", type=int, default=3, help="pre- and post-smoothing sweeps")
