@@ -40,7 +40,7 @@ EXTEND32_BYTES_BPLUS = 20
 EXTEND32_BYTES_B = 4
 # DRAM bytes (read + write) of one FP32 extension launch over B+ of the unit
 # sphere at dx = 1/256, from one ncu capture of the same kernel and workload.
-EXTEND32_TRAFFIC = 195.472128e6 + 27.053568e6
+EXTEND32_TRAFFIC = 165.8112e6 + 21.328128e6
 FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak is provided)
 
 
@@ -401,15 +401,15 @@ def run_cpm(args, world, rank, local):
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": nb * 8,
                 "d2h_bytes_per_step": nb * 8},
         "gpu_launches": int(launches),
-        "roofline": {"kernel": "k_extend_tiles<float,3> (FP32 extension over B+; 48 % of the "
-                               "mixed solve's kernel time)", "bound": "hbm",
+        "roofline": {"kernel": "k_extend_tiles<float,3> (FP32 extension over B+, the largest "
+                               "share of the mixed solve's kernel time)", "bound": "hbm",
                      "achieved": ach32, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
                      "frac": ach32 / pk.get("hbm_gbs", 6800.0),
                      "traffic": EXTEND32_TRAFFIC if wl["kind"] == "sphere" and wl["dx"] == DX else None,
                      "algorithmic_bytes": bytes32, "points": npl, "ms": ext32_ms,
                      "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"},
         "roofline_f64_extend": {"kernel": "k_extend_tiles<double,3> (FP64 extension of the outer "
-                                          "residual; 23 %)", "bound": "alu",
+                                          "residual)", "bound": "alu",
                                 "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                                 "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": None,
                                 "flops_per_point": EXTEND_FLOPS, "points": npl, "ms": ext64_ms,
