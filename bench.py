@@ -58,10 +58,14 @@ def _mixed_rhs(y):
 WORKLOADS = {
     "sphere256": {"kind": "sphere", "params": (), "dx": 1 / 256, "coarsest": 1 / 8, "rhs": _sphere_rhs,
                   "desc": "unit sphere dx=1/256, 23 N(0,1) harmonics l in {2,3,5}"},
+    # at dx = 1/512 the FP64 evaluation of f - A u has a relative floor of about
+    # 1e-10 (sphere) and 1.7e-10 (torus): both the FP64 and the mixed solver
+    # stall there, so these workloads stop at 3e-10
     "sphere512": {"kind": "sphere", "params": (), "dx": 1 / 512, "coarsest": 1 / 8, "rhs": _mixed_rhs,
-                  "desc": "unit sphere dx=1/512, f = (1 + 0.5 x y) u_rand"},
+                  "tol": 3e-10, "desc": "unit sphere dx=1/512, f = (1 + 0.5 x y) u_rand"},
     "torus512": {"kind": "torus", "params": (1.0, 0.4), "dx": 1 / 512, "coarsest": 1 / 16,
-                 "rhs": _mixed_rhs, "desc": "torus R=1 r=0.4 dx=1/512, f = (1 + 0.5 x y) u_rand"},
+                 "rhs": _mixed_rhs, "tol": 3e-10,
+                 "desc": "torus R=1 r=0.4 dx=1/512, f = (1 + 0.5 x y) u_rand"},
 }
 
 
@@ -230,8 +234,10 @@ def run_cpm(args, world, rank, local):
             import torch.distributed as dist
             dist.barrier()
 
+    tol = wl.get("tol", 1e-10)
+
     def solve(mode):
-        _, rep = H.solve(f, u, tol=1e-10, max_iter=200, mode=mode, zero_init=True,
+        _, rep = H.solve(f, u, tol=tol, max_iter=200, mode=mode, zero_init=True,
                          inner_cycles=args.inner)
         assert rep["converged"], rep
         return rep
@@ -340,7 +346,7 @@ def run_cpm(args, world, rank, local):
     ev0.record(st)
     for _ in range(args.steps):
         fd.copy_(f_host, non_blocking=True)
-        H.solve(fd, ud, tol=1e-10, max_iter=200, mode="mixed", zero_init=True,
+        H.solve(fd, ud, tol=tol, max_iter=200, mode="mixed", zero_init=True,
                 inner_cycles=args.inner)
         u_host.copy_(ud, non_blocking=True)
     ev1.record(st)
@@ -384,11 +390,13 @@ def run_cpm(args, world, rank, local):
     sweeps = 2 * args.nu * args.inner  # Jacobi sweeps per level per outer iteration
     updates = sum(sizes[:-1]) * sweeps * iters_mixed
     line = {
-        "metric": METRIC, "value": mixed_ms / 1e3, "unit": "s", "n_gpus": world,
+        "metric": METRIC if args.workload == "sphere256" else
+                  f"s to {tol:g} rel residual, {wl['desc']}: FP32-IR vs FP64",
+        "value": mixed_ms / 1e3, "unit": "s", "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": mixed_ms,
         "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32+f64", "data": "synthetic",
-        "config": {"workload": f"{wl['desc']} ({nb} band points, {band.ng} ghost), c=1, tol 1e-10, "
+        "config": {"workload": f"{wl['desc']} ({nb} band points, {band.ng} ghost), c=1, tol {tol:g}, "
                                "mixed FP32 V-cycle in FP64 defect correction",
                    "levels": sizes, "smoother": f"jacobi nu={args.nu}/{args.nu} omega={args.omega}",
                    "residual": args.residual, "inner_cycles": args.inner, "transfers": "linear",
