@@ -58,14 +58,10 @@ def _mixed_rhs(y):
 WORKLOADS = {
     "sphere256": {"kind": "sphere", "params": (), "dx": 1 / 256, "coarsest": 1 / 8, "rhs": _sphere_rhs,
                   "desc": "unit sphere dx=1/256, 23 N(0,1) harmonics l in {2,3,5}"},
-    # at dx = 1/512 the FP64 evaluation of f - A u has a relative floor of about
-    # 1e-10 (sphere) and 1.7e-10 (torus): both the FP64 and the mixed solver
-    # stall there, so these workloads stop at 3e-10
     "sphere512": {"kind": "sphere", "params": (), "dx": 1 / 512, "coarsest": 1 / 8, "rhs": _mixed_rhs,
-                  "tol": 3e-10, "desc": "unit sphere dx=1/512, f = (1 + 0.5 x y) u_rand"},
+                  "desc": "unit sphere dx=1/512, f = (1 + 0.5 x y) u_rand"},
     "torus512": {"kind": "torus", "params": (1.0, 0.4), "dx": 1 / 512, "coarsest": 1 / 16,
-                 "rhs": _mixed_rhs, "tol": 3e-10,
-                 "desc": "torus R=1 r=0.4 dx=1/512, f = (1 + 0.5 x y) u_rand"},
+                 "rhs": _mixed_rhs, "desc": "torus R=1 r=0.4 dx=1/512, f = (1 + 0.5 x y) u_rand"},
 }
 
 

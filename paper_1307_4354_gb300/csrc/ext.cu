@@ -343,9 +343,15 @@ __device__ __forceinline__ float contract(const float* base, const PointWeights<
 
 // One CTA per tile.  Shared memory: NZ*7 box rows, each 4 windows of 4
 // values plus one pad window (row stride 20 values spreads rows over banks).
-template <typename T, int DIM>
+// REL (FP64 residual form): the tile's values are staged relative to one
+// reference value (u at the first band node of the base brick), the kernel
+// writes delta_j = (E u)_j - ref and ref_j = ref.  The subtraction comes before
+// the weighted sum, so delta carries rounding errors relative to the small
+// differences only, not to |u|.
+template <typename T, int DIM, bool REL = false>
 __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, const T* __restrict__ u,
-                                                              T* __restrict__ w, bool with_ghost) {
+                                                              T* __restrict__ w, bool with_ghost,
+                                                              T* __restrict__ refv) {
   constexpr int NZ = DIM == 3 ? 7 : 1;
   constexpr int RS = 20;
   constexpr int NB = DIM == 3 ? 8 : 4;  // bricks overlapping the box
@@ -376,6 +382,7 @@ __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, co
     sm_start[j][1] = s0 + __popc((uint32_t)m);
   }
   __syncthreads();
+  const T ref = REL ? __ldg(u + sm_start[0][0]) : T(0);
   // stage the nodes the tile's stencils read: bases span [lo, hi] per axis,
   // so box nodes lo .. hi+3.  Thread r owns box row (y, z): it reads the
   // row's band nodes in order (consecutive band indices within each of the
@@ -404,7 +411,10 @@ __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, co
         v[i] = T(0);
         if (x <= xhi + 3) {
           const bool hi = x >= 4;
-          if (((hi ? rbb : rba) >> (x & 3)) & 1u) v[i] = __ldg(u + (hi ? cb++ : ca++));
+          if (((hi ? rbb : rba) >> (x & 3)) & 1u) {
+            v[i] = __ldg(u + (hi ? cb++ : ca++));
+            if (REL) v[i] -= ref;
+          }
         }
       }
       T* row = win + (z * 7 + y) * RS;
@@ -417,6 +427,7 @@ __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, co
   for (; k < end; k += kExtThreads) {
     const T* base = win + ((rec >> 4) & 3) * 7 * RS + ((rec >> 2) & 3) * RS + (rec & 3) * 4;
     w[rec >> 6] = contract<DIM>(base, pw);
+    if (REL) refv[rec >> 6] = ref;
     const int32_t kn = k + kExtThreads;
     if (kn < end) {
       rec = __ldg(L.erec + kn);
@@ -432,9 +443,20 @@ void launch_extend(const LevelView<T>& L, const T* u, T* w, int32_t npts, cudaSt
   if (nt <= 0) return;
   const bool with_ghost = npts > L.nB;
   if (L.dim == 3)
-    k_extend_tiles<T, 3><<<nt, kExtThreads, 0, st>>>(L, u, w, with_ghost);
+    k_extend_tiles<T, 3><<<nt, kExtThreads, 0, st>>>(L, u, w, with_ghost, nullptr);
   else
-    k_extend_tiles<T, 2><<<nt, kExtThreads, 0, st>>>(L, u, w, with_ghost);
+    k_extend_tiles<T, 2><<<nt, kExtThreads, 0, st>>>(L, u, w, with_ghost, nullptr);
+  count_launch();
+}
+
+void launch_extend_rel(const LevelView<double>& L, const double* u, double* delta, double* refv,
+                       cudaStream_t st) {
+  const int32_t nt = L.ntiles;
+  if (nt <= 0) return;
+  if (L.dim == 3)
+    k_extend_tiles<double, 3, true><<<nt, kExtThreads, 0, st>>>(L, u, delta, true, refv);
+  else
+    k_extend_tiles<double, 2, true><<<nt, kExtThreads, 0, st>>>(L, u, delta, true, refv);
   count_launch();
 }
 

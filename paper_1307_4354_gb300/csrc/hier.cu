@@ -173,6 +173,7 @@ struct Workspace {
   double* norms = nullptr;
   cpm::DBuf<double> normf;  // norms of f
   cpm::DBuf<double> u_own, f_own, r64, d64;
+  cpm::DBuf<double> refv;   // per point of the finest B+: the extension's reference value
   cpm::DBuf<float> r32, d32;
   cudaStream_t hs = nullptr;
   cudaEvent_t ev = nullptr;
@@ -230,6 +231,7 @@ static void alloc_workspace(const cpm_hier_s& H, Workspace& W, double* norms_slo
   W.f_own.alloc(nB0);
   W.r64.alloc(nB0);
   W.d64.alloc(nB0);
+  W.refv.alloc(H.L[0].lev->nplus());
   W.r32.alloc(nB0);
   W.d32.alloc(nB0);
   CPM_CUDA_TRY(cudaStreamCreateWithFlags(&W.hs, cudaStreamNonBlocking));
@@ -381,14 +383,15 @@ static void vcycle_level(cpm_hier_s* H, Workspace& W, int l, const T* f, T* u, c
   vcycle_level<T>(H, &w, 1, l, &f, &u, st);
 }
 
-// FP64 outer residual r = f - A u on the finest level with norms into H->norms.
+// FP64 outer residual r = f - A u on the finest level with norms into W.norms,
+// in the relative form (differences formed from exact inputs; its rounding
+// floor is far below that of w = E u followed by the stencil at fine dx).
 static void outer_residual(cpm_hier_s* H, Workspace& W, const double* f, const double* u, double* r,
                            cudaStream_t st) {
   HLevel& lv = H->L[0];
   const LevelView<double> v = lv.view<double>();
-  launch_extend<double>(v, u, W.w64[0].w.get(), (int32_t)v.nplus, st);
-  launch_lap<double>(v, LAP_RESID, u, W.w64[0].w.get(), f, lv.c64.get(), H->c, nullptr, 0.0, r, nullptr,
-                     W.part.get(), W.part_blocks, st);
+  launch_extend_rel(v, u, W.w64[0].w.get(), W.refv.get(), st);
+  launch_resid_rel(v, u, W.w64[0].w.get(), W.refv.get(), f, lv.c64.get(), H->c, r, W.part.get(), st);
   launch_norm_final(W.part.get(), nblk(v.nB, 256), W.norms, st);
 }
 

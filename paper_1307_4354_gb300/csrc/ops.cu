@@ -69,22 +69,32 @@ template <typename T, int DIM, int MODE>
 __global__ void __launch_bounds__(256) k_lap(LevelView<T> L, const T* u, const T* __restrict__ w,
                                              const T* __restrict__ f, const T* __restrict__ cvec,
                                              T cval, const T* __restrict__ dA, T omega, T* out,
-                                             T* u_inout, double* part) {
+                                             T* u_inout, double* part, const T* __restrict__ refv) {
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   double rm = 0.0, rs = 0.0;
   if (i < L.nB) {
     const T wi = w[i];
-    T s = T(0);
-#pragma unroll
-    for (int q = 0; q < 2 * DIM; ++q) s += w[__ldg(L.nbr + (int64_t)q * L.nB + i)] - wi;
     const T ui = u[i];
-    const T Mu = s * L.inv_h2 + L.gamma * (wi - ui);
+    T s = T(0), Mu;
+    if (MODE == LAP_RESID_REL) {
+      const T ri = refv[i];
+#pragma unroll
+      for (int q = 0; q < 2 * DIM; ++q) {
+        const int32_t k = __ldg(L.nbr + (int64_t)q * L.nB + i);
+        s += (refv[k] - ri) + (w[k] - wi);
+      }
+      Mu = s * L.inv_h2 + L.gamma * ((ri - ui) + wi);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 2 * DIM; ++q) s += w[__ldg(L.nbr + (int64_t)q * L.nB + i)] - wi;
+      Mu = s * L.inv_h2 + L.gamma * (wi - ui);
+    }
     if (MODE == LAP_APPLY) {
       out[i] = Mu;
     } else {
       const T c = cvec ? cvec[i] : cval;
       const T r = f[i] - c * ui + Mu;
-      if (MODE == LAP_RESID) {
+      if (MODE == LAP_RESID || MODE == LAP_RESID_REL) {
         out[i] = r;
         rm = fabs((double)r);
         rs = (double)r * (double)r;
@@ -93,7 +103,7 @@ __global__ void __launch_bounds__(256) k_lap(LevelView<T> L, const T* u, const T
       }
     }
   }
-  if (MODE == LAP_RESID && part) block_max_sum(rm, rs, part);
+  if ((MODE == LAP_RESID || MODE == LAP_RESID_REL) && part) block_max_sum(rm, rs, part);
 }
 
 template <int DIM, int MODE, typename T>
@@ -101,7 +111,7 @@ static void lap_dispatch(const LevelView<T>& L, const T* u, const T* w, const T*
                          T cval, const T* dA, T omega, T* out, T* u_inout, double* part,
                          cudaStream_t st) {
   k_lap<T, DIM, MODE><<<nblk(L.nB, 256), 256, 0, st>>>(L, u, w, f, cvec, cval, dA, omega, out,
-                                                         u_inout, part);
+                                                         u_inout, part, nullptr);
   count_launch();
 }
 
@@ -120,6 +130,19 @@ void launch_lap(const LevelView<T>& L, LapMode mode, const T* u, const T* w, con
     if (mode == LAP_RESID) lap_dispatch<2, LAP_RESID>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, st);
     if (mode == LAP_JACOBI) lap_dispatch<2, LAP_JACOBI>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, st);
   }
+}
+
+void launch_resid_rel(const LevelView<double>& L, const double* u, const double* delta,
+                      const double* refv, const double* f, const double* cvec, double cval,
+                      double* r, double* part, cudaStream_t st) {
+  if (L.nB <= 0) return;
+  if (L.dim == 3)
+    k_lap<double, 3, LAP_RESID_REL><<<nblk(L.nB, 256), 256, 0, st>>>(
+        L, u, delta, f, cvec, cval, nullptr, 0.0, r, nullptr, part, refv);
+  else
+    k_lap<double, 2, LAP_RESID_REL><<<nblk(L.nB, 256), 256, 0, st>>>(
+        L, u, delta, f, cvec, cval, nullptr, 0.0, r, nullptr, part, refv);
+  count_launch();
 }
 
 // ----------------------------------------------------------------- Ruuth-Merriman

@@ -41,11 +41,24 @@ struct TransferView {
   int dim;
 };
 
-enum LapMode { LAP_APPLY = 0, LAP_RESID = 1, LAP_JACOBI = 2 };
+enum LapMode { LAP_APPLY = 0, LAP_RESID = 1, LAP_JACOBI = 2, LAP_RESID_REL = 3 };
 
 // w = E u on the first npts points of B+ (npts = nB or nB + nG).
 template <typename T>
 void launch_extend(const LevelView<T>& L, const T* u, T* w, int32_t npts, cudaStream_t st);
+
+// FP64 extension over B+ in relative form: delta_j = (E u)_j - ref_j with
+// ref_j = u at a reference node of j's tile (see k_extend_tiles).
+void launch_extend_rel(const LevelView<double>& L, const double* u, double* delta, double* refv,
+                       cudaStream_t st);
+// FP64 residual r = f - c u + M u from the relative extension: every
+// difference w_k - w_i = (ref_k - ref_i) + (delta_k - delta_i) and
+// w_i - u_i = (ref_i - u_i) + delta_i is formed from exact inputs, so the
+// rounding floor is relative to the differences, not to |u| / dx^2.  Per-block
+// partial (max|r|, sum r^2) into part (nblk(nB, 256) blocks).
+void launch_resid_rel(const LevelView<double>& L, const double* u, const double* delta,
+                      const double* refv, const double* f, const double* cvec, double cval,
+                      double* r, double* part, cudaStream_t st);
 
 // Stencil pass on B from w = E u:
 //   APPLY : out = M u
