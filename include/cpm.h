@@ -305,7 +305,13 @@ cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opt
 
 /*
  * r = f - A u on the finest level in FP64 (the outer residual of cpm_solve,
- * difference form of M).  f, u, r: FP64 device vectors of length |B_0|.
+ * difference form of M, Eq. 2.10).  Evaluated in relative form: the
+ * extension of each tile works on u - u_ref (u_ref = u at one band node of
+ * the tile) and the stencil combines reference differences and extension
+ * differences formed from exact inputs, so the rounding error scales with
+ * local differences of u rather than |u|/dx^2 (the plain form has a relative
+ * floor near 1e-10 at dx = 1/512).  f, u, r: FP64 device vectors of length
+ * |B_0|.  cpm_residual_norms uses the same evaluation.
  */
 cpm_status cpm_residual(cpm_hier h, const double* f, const double* u, double* r, cpm_stream stream);
 
