@@ -49,3 +49,23 @@ def test_no_oracle_in_product_path():
             if f.endswith((".py", ".cu", ".cuh", ".h")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt, f
+
+
+def test_null_handles_are_rejected_without_a_gpu():
+    """Every entry point checks its handles before any device work: NULL gives
+    CPM_ERR_ARG with a message, destroy(NULL) is a no-op (CPU only)."""
+    import ctypes as C
+    import paper_1307_4354_gb300 as pkg
+    pkg.build()
+    L = pkg.capi.lib()
+    ERR_ARG = pkg.capi.CPM_ERR_ARG
+    out = C.c_void_p()
+    assert L.cpm_build_hierarchy(None, None, None, C.byref(out)) == ERR_ARG
+    assert L.cpm_solve(None, None, None, None, None, None) == ERR_ARG
+    assert L.cpm_residual_norms_noalloc(None, None, None, None, None) == ERR_ARG
+    assert L.cpm_build_batch(None, 0, 1, None, C.byref(out)) == ERR_ARG
+    assert L.cpm_build_batch(None, 1, 0, None, C.byref(out)) == ERR_ARG
+    assert L.cpm_solve_batch(None, None, None, None, None, None) == ERR_ARG
+    assert L.cpm_batch_info(None, None, None) == ERR_ARG
+    assert L.cpm_last_error()
+    assert L.cpm_batch_destroy(None) == pkg.capi.CPM_OK
