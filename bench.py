@@ -401,6 +401,8 @@ def run_cpm(args, world, rank, local):
         "iters_mixed": iters_mixed, "fp64_s": f64_ms / 1e3, "iters_fp64": reps64[-1]["iters"],
         "learned": learned,
         "band_point_updates_per_s": updates / (mixed_ms * 1e-3),
+        "vcycles_per_s": {"mixed_fp32": iters_mixed * args.inner / (mixed_ms * 1e-3),
+                          "fp64": reps64[-1]["iters"] / f64_ms * 1e3},
         "setup_s": setup_s,
         "e2e": {"value": e2e_ms / 1e3, "unit": "s", "h2d_bytes_per_step": nb * 8,
                 "d2h_bytes_per_step": nb * 8},
@@ -516,6 +518,7 @@ def run_batch(args, world, rank, local):
         "sequential_s": seq_ms / 1e3, "sequential_iters_equal": seq_iters == iters,
         "band_point_updates_per_s": sum(sizes[s // n_rhs] * iters[s] for s in range(len(fs)))
         * 2 * args.inner * args.nu / (batch_ms * 1e-3),
+        "vcycles_per_s": sum(iters) * args.inner / (batch_ms * 1e-3),
         "setup_s": setup_s, "gpu_launches": int(launches), "clocks": clk.summary(),
     }
     print(json.dumps(line), flush=True)
