@@ -102,3 +102,25 @@ def test_coarsest_solve_is_direct():
     from oracle.multigrid import coarse_solve
     u = coarse_solve(H, f)
     assert np.abs(lev.ops.A_matrix(lev.c) @ u - f).max() < 1e-10 * np.abs(f).max()
+
+
+def test_vcycle_rate_with_relaxed_coarse_level():
+    """Ellipsoid (1.05, 0.9, 0.8), reach 0.61: the level dx = 1/8 violates the
+    strict coarsening rule ((lambda + 1)/8 = 0.64 > reach) but its band lies
+    within the reach (sqrt(17)/8 = 0.52) and builds; as the coarse level of a
+    two-level V-cycle from dx = 1/16 it keeps the contraction near 0.1."""
+    from oracle.geometry import ellipsoid
+    surf = ellipsoid(1.05, 0.9, 0.8)
+    assert (np.sqrt(17) + 1) / 8 > surf.reach > np.sqrt(17) / 8
+    H = build_hierarchy(surf, 1 / 16, 1 / 8,
+                        opts=MGOptions(nu1=3, nu2=3, omega=0.8, smoother="jacobi", residual="plain"))
+    fine = H.levels[0]
+    f = synth.harmonic_field(fine.band.cp[: fine.band.nb], seed=1)
+    u = np.zeros_like(f)
+    norms = []
+    for _ in range(6):
+        r = f - fine.ops.apply_A(u, fine.c)
+        norms.append(np.abs(r).max())
+        u = u + vcycle(H, np.zeros_like(f), r)
+    rates = np.asarray(norms[1:]) / np.asarray(norms[:-1])
+    assert np.all(rates < 0.15), rates
