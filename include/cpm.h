@@ -385,8 +385,15 @@ cpm_status cpm_residual_norms(cpm_hier h, const double* f, const double* u, doub
  * work being recorded into a CUDA graph by stream capture (cudaMalloc is
  * refused during a global-mode capture), loops with hard latency budgets that
  * forbid allocator calls, and frameworks that hand out all device memory from
- * their own pool.  It computes r = f - A u on the finest level (FP64,
- * difference form, as cpm_residual_norms) and writes norms[0] = max_i |r_i|
+ * their own pool.  It computes r = f - A u on the finest level in FP64 in the
+ * direct form (w = E u, then the stencil on w and u; unlike cpm_residual_norms,
+ * which uses the relative form described at cpm_residual).  Its rounding floor
+ * is that of the direct form, about 6 eps |u| / dx^2 in absolute terms; on the
+ * levels it accepts (at most 1048576 band + ghost points, dx >= 1/128 for the
+ * unit sphere) that is below 1e-12 |M u| for smooth u, so near a converged
+ * solution the max |r_i| of the two entry points may differ by up to about
+ * 1e-12 max |f_i|.  It writes
+ * norms[0] = max_i |r_i|
  * and norms[1] = sum_i r_i^2 to the DEVICE pointer `norms` (2 doubles,
  * asynchronously on `stream`; nothing is copied to the host).  f, u: FP64
  * device vectors of length |B_0|.
@@ -396,7 +403,9 @@ cpm_status cpm_residual_norms(cpm_hier h, const double* f, const double* u, doub
  * of CPM_NOALLOC_MAX_POINTS doubles plus 8192 doubles (about 8.1 MB), held on
  * every GPU that loads the library until the process exits.  The first call
  * on a device (with that device current) looks up the array's device address
- * once; make that first call before any stream capture.  Every call shares
+ * once; make that first call before any stream capture.  The looked-up
+ * address is cached with the id of the CUDA context that was current, so after
+ * cudaDeviceReset (a new context) the next call looks it up again.  Every call shares
  * the one array and overwrites it: calls whose kernels overlap on the GPU
  * (other streams, other host threads) race and must be serialised by the
  * caller.  Nothing in the scratch needs to start at zero.

@@ -10,6 +10,8 @@
 // device array of fixed size, resident on every GPU that loads the library
 // until the process exits.  The paper has no counterpart; it is plumbing
 // around the residual r = f - A u of the discrete system.
+#include <cuda.h>
+
 #include <mutex>
 
 #include "ops.cuh"
@@ -83,20 +85,52 @@ __global__ void k_final_noalloc(const double* part, int nblocks, double* norms) 
   }
 }
 
-// Device address of the scratch array, resolved once per device (host code
-// cannot pass the symbol itself to a kernel: in host code it names a host-side
-// stand-in, not device memory).
+// Device address of the scratch array for the calling thread's current
+// context (host code cannot pass the symbol itself to a kernel: in host code
+// it names a host-side stand-in, not device memory).  The address is looked up
+// with cudaGetSymbolAddress on the first call in a context and cached with the
+// context's unique id (cuCtxGetId), so a context torn down and created again
+// (cudaDeviceReset) gets a fresh lookup instead of a dangling address.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+static uint64_t current_context_id() {
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(f);
+    f = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &f, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess && q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(f);
+  });
+  CPM_CHECK(get_current && get_id, CPM_ERR_CUDA, "driver entry points cuCtxGetCurrent/cuCtxGetId unavailable");
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return 0;
+  unsigned long long id = 0;
+  if (get_id(ctx, &id) != CUDA_SUCCESS) return 0;
+  return (uint64_t)id + 1;  // 0 is reserved for "no valid context"
+}
+
 static double* scratch_address() {
   static std::mutex mu;
+  static uint64_t ctx_of[128] = {0};
   static double* addr[128] = {nullptr};
   int dev = 0;
   CPM_CUDA_TRY(cudaGetDevice(&dev));
   CPM_CHECK(dev >= 0 && dev < 128, CPM_ERR_ARG, "device ordinal out of range");
   std::lock_guard<std::mutex> lock(mu);
-  if (!addr[dev]) {
+  const uint64_t id = current_context_id();
+  if (id == 0 || id != ctx_of[dev] || !addr[dev]) {
     void* p = nullptr;
-    CPM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+    CPM_CUDA_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));  // makes the context current
     addr[dev] = static_cast<double*>(p);
+    ctx_of[dev] = current_context_id();
   }
   return addr[dev];
 }
