@@ -94,9 +94,10 @@ def _round_sphere(X: np.ndarray, R: float):
         r = np.sqrt((X[:, 0] * X[:, 0] + X[:, 1] * X[:, 1]) + X[:, 2] * X[:, 2])
     d = r - R
     dist2 = d * d
+    # the centre (r = 0) has no closest point: t = inf there and cp = 0 * inf = nan
     with np.errstate(divide="ignore", invalid="ignore"):
         t = R / r
-    cp = X * t[:, None]
+        cp = X * t[:, None]
     return cp, dist2
 
 
@@ -107,11 +108,12 @@ def _torus(X: np.ndarray, R: float, r: float):
     q = np.sqrt(a * a + z * z)
     d = q - r
     dist2 = d * d
+    # the axis (rho = 0) and the centre circle (q = 0) have no closest point (nan)
     with np.errstate(divide="ignore", invalid="ignore"):
         s = r / q
         m = R + a * s
         k = m / rho
-    cp = np.stack([x * k, y * k, z * s], axis=1)
+        cp = np.stack([x * k, y * k, z * s], axis=1)
     return cp, dist2
 
 
@@ -133,10 +135,13 @@ def _ellipsoid_t(X: np.ndarray, axes: np.ndarray, iters: int = 1100) -> np.ndarr
         mid = 0.5 * (lo + hi)
         if np.all((mid == lo) | (mid == hi)):
             break
-        g0 = ax[:, 0] / (a2[0] + mid)
-        g1 = ax[:, 1] / (a2[1] + mid)
-        g2 = ax[:, 2] / (a2[2] + mid)
-        F = ((g0 * g0 + g1 * g1) + g2 * g2) - 1.0
+        # a collapsed bracket at -min a_i^2 with x_i = 0 gives 0/0 = nan there:
+        # F > 0 is then false, so the node stays marked as never moved
+        with np.errstate(divide="ignore", invalid="ignore"):
+            g0 = ax[:, 0] / (a2[0] + mid)
+            g1 = ax[:, 1] / (a2[1] + mid)
+            g2 = ax[:, 2] / (a2[2] + mid)
+            F = ((g0 * g0 + g1 * g1) + g2 * g2) - 1.0
         pos = F > 0
         moved |= pos
         lo = np.where(pos, mid, lo)

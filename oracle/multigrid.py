@@ -90,15 +90,19 @@ def coarsest_spacing_ok(surface: Surface, dx: float, lambda2: float) -> bool:
 
 def build_hierarchy(surface: Surface, dx: float, coarsest_dx: float, c=1.0,
                     opts: MGOptions | None = None, c_fn=None) -> Hierarchy:
-    """Levels dx, 2dx, .., coarsest_dx.  ``c_fn(cp) -> c`` gives a variable c."""
+    """Levels dx, 2dx, .., coarsest_dx.  ``c_fn(cp) -> c`` gives a variable c.
+
+    A variable c is c_fn(cp(x)) on the finest band; coarser levels carry the
+    restriction of the finer level's c (linear interpolation at their closest
+    points), the reading that needs c only on the finest band.
+    """
     opts = opts or MGOptions()
     levels = []
     h = dx
     while True:
         band = build_band(surface, h, p=opts.p)
         ops = Operators(band, opts.p)
-        cvec = c_fn(band.cp[: band.nb]) if c_fn is not None else np.full(band.nb, float(c))
-        levels.append(Level(band, ops, cvec))
+        levels.append(Level(band, ops, np.full(band.nb, float(c))))
         if h >= coarsest_dx * (1 - 1e-12):
             break
         h *= 2.0
@@ -106,6 +110,13 @@ def build_hierarchy(surface: Surface, dx: float, coarsest_dx: float, c=1.0,
         fine, coarse = levels[l], levels[l + 1]
         fine.R = interp_matrix(fine.band, coarse.band.cp[: coarse.band.nb], opts.transfer_p)
         fine.P = interp_matrix(coarse.band, fine.band.cp[: fine.band.nb], opts.transfer_p)
+    if c_fn is not None:
+        # c is a surface function (footnote to Sec. 2.1) known on the finest band
+        # as c(cp(x)); each coarser level takes it at its own closest points by
+        # the restriction of Sec. 4.3 (interpolation at cp from the finer band).
+        levels[0].c = np.asarray(c_fn(levels[0].band.cp[: levels[0].band.nb]), dtype=np.float64)
+        for l in range(len(levels) - 1):
+            levels[l + 1].c = levels[l].R @ levels[l].c
     for lev in levels:
         lev.diagA = lev.c - lev.ops.diag_M()
     hier = Hierarchy(levels, opts)

@@ -124,3 +124,25 @@ def test_vcycle_rate_with_relaxed_coarse_level():
         u = u + vcycle(H, np.zeros_like(f), r)
     rates = np.asarray(norms[1:]) / np.asarray(norms[:-1])
     assert np.all(rates < 0.15), rates
+
+
+def test_variable_c_restricted_to_coarse_levels():
+    """Variable c (a surface function, footnote to Sec. 2.1): the finest level
+    holds c(cp(x)); each coarser level holds the restriction of the finer c
+    (interpolation at its own closest points, Sec. 4.3).  That restriction
+    reproduces c(cp) on the coarse band to O(dx^2), and the V-cycle solution
+    is still the direct solution of diag(c) u - M u = f on the finest band."""
+    c_fn = lambda y: 1.0 + 0.5 * np.sin(2 * np.pi * y[:, 2])
+    H = build_hierarchy(sphere(), 1 / 16, 1 / 8,
+                        opts=MGOptions(smoother="jacobi", nu1=3, nu2=3, omega=0.8), c_fn=c_fn)
+    fine, coarse = H.levels
+    assert np.array_equal(fine.c, c_fn(fine.band.cp[: fine.band.nb]))
+    assert np.array_equal(coarse.c, fine.R @ fine.c)
+    # linear interpolation error of a smooth cp-extended field at spacing 1/16
+    assert np.abs(coarse.c - c_fn(coarse.band.cp[: coarse.band.nb])).max() < 0.05
+    assert not np.allclose(coarse.c, c_fn(coarse.band.cp[: coarse.band.nb]), rtol=0, atol=1e-12)
+    _, f = synth.sphere_harmonics(fine.band.cp[: fine.band.nb])
+    u, rep = solve(H, f, tol=1e-12, max_iter=60)
+    assert rep.converged and rep.iters <= 20
+    ud = spla.spsolve(fine.ops.A_matrix(fine.c).tocsc(), f)
+    assert np.abs(u - ud).max() <= 1e-10 * np.abs(ud).max()
