@@ -344,15 +344,13 @@ def run_cpm(args, world, rank, local):
     if not args.no_learned and args.workload == "sphere256":
         from paper_1307_4354_gb300 import train as tr
         t0 = time.perf_counter()
-        sets = [tr.residual_fields(kind, prm, 1 / 64, seed=i)
-                for i, (kind, prm) in enumerate(tr.training_surfaces(0, 3, 2))]
+        sets = tr.training_set(seed=0, spacings=(1 / 64, 1 / 96, 1 / 128))
+        data_s = time.perf_counter() - t0
         sm = pkg.Smoother(0)
-        for h, _ in sets:
-            h.set_smoother(sm)
-        loss0 = tr.mean_loss(sets)
-        tr.train(sm, sets, steps=args.train_steps, lr=2e-3)
-        loss1 = tr.mean_loss(sets)
-        train_s = time.perf_counter() - t0
+        trep = tr.train(sm, sets, steps=args.train_steps, lr=2e-3, lr_final=2e-4)
+        loss0, loss1 = trep["loss_first"], trep["loss_last"]
+        train_s = trep["seconds"]
+        train_points = [h.nb for h, _ in sets]
         del sets
         H.set_smoother(sm)
 
@@ -392,6 +390,7 @@ def run_cpm(args, world, rank, local):
         learned = {"s": learned_ms / 1e3, "iters": repsL[-1]["iters"],
                    "fallback": repsL[-1]["fallback"], "jacobi_factor": repsL[-1]["jacobi_factor"],
                    "learned_factor": repsL[-1]["learned_factor"], "train_s": train_s,
+                   "train_data_s": data_s, "train_points": train_points,
                    "train_steps": args.train_steps, "train_loss": [loss0, loss1],
                    "torus_r035_dx256_variable_c": ev, "torus_points": Ht.nb}
         H.set_smoother(None)

@@ -65,7 +65,11 @@ typedef enum cpm_surface_kind {
   CPM_CIRCLE = 0,    /* d = 2, param[0] = radius R (centre at the origin)     */
   CPM_SPHERE = 1,    /* d = 3, param[0] = radius R                             */
   CPM_TORUS = 2,     /* d = 3, about the z axis: param[0] = R, param[1] = r    */
-  CPM_ELLIPSOID = 3  /* d = 3, semi-axes param[0..2]                           */
+  CPM_ELLIPSOID = 3, /* d = 3, semi-axes param[0..2]                           */
+  CPM_DZIUK = 4      /* d = 3, the level set (x1 - x3^2)^2 + x2^2 + x3^2 = 1 of
+                        Sec. 4.5.5; cp by Newton's method on the Lagrange
+                        conditions (30 steps from the node); reach 0.0957, so
+                        bands need dx <= 1/64 on the [-2, 2] grid           */
 } cpm_surface_kind;
 
 /* A closed surface with a closed-form or Newton closest point (Sec. 2.1). */
@@ -116,14 +120,33 @@ cpm_status cpm_band_info(cpm_band band, int64_t* n_band, int64_t* n_ghost);
  */
 cpm_status cpm_band_export(cpm_band band, int32_t* ijk, double* cp, int32_t* stencil_base);
 
+/*
+ * The sizes Table 4.1 reports for a band, counted on the device: counts[0] =
+ * |B|, counts[1] = nnz(L) of the 2d+1-point Laplacian restricted to B
+ * (out-of-band neighbours dropped), counts[2] = nnz(E_3) = |B| 4^d, counts[3]
+ * = nnz(M) of M = E_1 L - gamma (I - E_3) (Eq. 3.3): the cubic stencil pattern
+ * plus one diagonal entry for every node outside its own stencil.  counts:
+ * HOST array of 4 int64.  Synchronous.
+ */
+cpm_status cpm_band_counts(cpm_band band, int64_t* counts, cpm_stream stream);
+
 cpm_status cpm_band_destroy(cpm_band band);
 
 /* ---------------------------------------------------------------- hierarchy */
 
 typedef enum cpm_smoother {
   CPM_SMOOTH_JACOBI = 0, /* weighted Jacobi on A (Eq. 4.1, Sec. 4.4)            */
-  CPM_SMOOTH_RM = 1      /* Ruuth-Merriman: Jacobi on cI - L, then u := E u
+  CPM_SMOOTH_RM = 1,     /* Ruuth-Merriman: Jacobi on cI - L, then u := E u
                             (Eq. 4.2, Sec. 4.2)                                 */
+  CPM_SMOOTH_RBGS = 2    /* Gauss-Seidel on A in red-black order (the
+                            alternative named in Sec. 4.4): the weighted Jacobi
+                            update of the red nodes (even i+j+k), then that of
+                            the black nodes from a fresh extension.  The
+                            interpolation stencils couple nodes of one colour,
+                            so this is not an exact Gauss-Seidel sweep; on the
+                            closest-point operators it does not make the
+                            defect correction converge (measured contraction
+                            above 0.5 per cycle, often above 1)               */
 } cpm_smoother;
 
 typedef enum cpm_prec { CPM_F64 = 0, CPM_F32 = 1 } cpm_prec;
@@ -141,7 +164,8 @@ typedef struct cpm_mg_opts {
   int32_t nu1, nu2;     /* pre / post smoothing sweeps (0: 3 and 3)             */
   double omega;         /* Jacobi weight (0: 0.8)                               */
   int32_t smoother;     /* cpm_smoother                                         */
-  int32_t transfer_deg; /* 1 (linear, Sec. 4.5) or 3 (0: 1)                     */
+  int32_t transfer_deg; /* restriction / prolongation interpolation degree:
+                           1 (linear, Sec. 4.5) or 3 (cubic) (0: 1)            */
   double c;             /* constant shift c > 0 (used when c_device is NULL)    */
   const double* c_device; /* optional per-point c on the finest band (device,
                              length n_band); coarse levels take c(cp) by
@@ -157,7 +181,28 @@ typedef struct cpm_mg_opts {
   int32_t coarse_f64_max;   /* 0: 16384 (the FP64 inverse costs 8 n^2 bytes)   */
   int32_t coarse_dense_max; /* 0: 40000 (the FP32 inverse costs 4 n^2 bytes);
                                at most 65536                                    */
+  int32_t op_form;          /* discrete operator M on every level:
+                               CPM_OP_MBR (0): diag(L) + (L - diag L) E, cubic E
+                               in both terms (Eq. 2.10, Remark 3.2);
+                               CPM_OP_PAPER (1): the paper's scheme
+                               E_1 L_B - gamma (I - E_3) with L_B the
+                               band-restricted Laplacian (Sec. 3.1 Eq. 3.3,
+                               Theorem 3.3);
+                               CPM_OP_VARDIFF (2): variable diffusion
+                               -div_S(a grad_S u) + c u = f (Sec. 4.5.6):
+                               E_1 L~ - diag(gamma a)(I - E_3) with
+                               L~ = sum over axes of D^b diag(A^f a) D^f on B
+                               and a from a_device (smoothing on A only)       */
+  int32_t cycle;            /* coarse-grid corrections per level: 1 V-cycle
+                               (Algorithm 4.1), 2 W-cycle (the remark at
+                               Algorithm 4.1; the second from the first's
+                               result) (0: 1)                                   */
+  const double* a_device;   /* CPM_OP_VARDIFF: the diffusion coefficient a(cp(x))
+                               > 0 on the finest band (device, length n_band);
+                               coarse levels take its restriction, like c      */
 } cpm_mg_opts;
+
+typedef enum cpm_op_form { CPM_OP_MBR = 0, CPM_OP_PAPER = 1, CPM_OP_VARDIFF = 2 } cpm_op_form;
 
 typedef struct cpm_hier_s* cpm_hier;
 
@@ -176,9 +221,10 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts,
 cpm_status cpm_hier_info(cpm_hier h, int32_t* n_levels, int32_t level, int64_t* n_band);
 
 /*
- * Mu = M u on level `level` (0 = finest): w = E u on B+, then
+ * Mu = M u on level `level` (0 = finest).  CPM_OP_MBR: w = E u on B+, then
  * (Mu)_i = sum_{k in N(i)} (w_k - w_i)/dx^2 + gamma (w_i - u_i),
- * gamma = 2d/dx^2 (spec operator, Sec. 2.3 Eq. 2.10).
+ * gamma = 2d/dx^2 (Sec. 2.3 Eq. 2.10).  CPM_OP_PAPER: v = L_B u on B, w = E_3 u
+ * on B, (Mu)_i = (E_1 v)_i - gamma (u_i - w_i) (Sec. 3.1 Eq. 3.3).
  * u, Mu: device vectors of length |B_level|, type per prec.
  */
 cpm_status cpm_apply(cpm_hier h, int32_t level, int32_t prec, const void* u, void* Mu,
@@ -254,6 +300,61 @@ cpm_status cpm_mlp_loss_grad(cpm_hier h, const float* r, double* loss, float* gr
  * output (may be NULL; reading it synchronises). */
 cpm_status cpm_mlp_train_step(cpm_hier h, const float* r, float lr, double* loss, cpm_stream stream);
 
+/*
+ * A training set for cpm_mlp_train: n_fields residual fields, field k living
+ * on the finest level of hier[k] (hierarchies may repeat).  r[k]: FP64 DEVICE
+ * vector of |B_0| of hier[k] (caller-owned, read only).  Each field is scaled
+ * by 1 / max_i |r_i| and cast to FP32 inside the library before training.
+ */
+typedef struct cpm_train_set {
+  int32_t n_fields;
+  const cpm_hier* hier;
+  const double* const* r;
+} cpm_train_set;
+
+typedef struct cpm_train_opts {
+  int32_t steps;     /* Adam steps in all (0: 400)                             */
+  float lr;          /* learning rate of the first step (0: 2e-3)              */
+  float lr_final;    /* learning rate of the last step; linear in between
+                        (0: equal to lr, a constant rate)                      */
+  int32_t reset;     /* 1: clear the Adam moments and step count first        */
+} cpm_train_opts;
+
+typedef struct cpm_train_report {
+  int32_t steps;     /* Adam steps taken                                       */
+  int32_t n_fields;
+  double loss_first; /* mean loss over the fields before the first step       */
+  double loss_last;  /* mean loss over the fields after the last step         */
+  double seconds;    /* wall time of the call                                 */
+} cpm_train_report;
+
+/*
+ * Train m on a set of residual fields of the method's own V-cycles (the
+ * learned smoother has no counterpart in the paper).  The library scales each
+ * FP64 field by 1 / max|r| into FP32, makes m the learned smoother of every
+ * hierarchy in the set (as cpm_hier_set_smoother), then runs opts->steps Adam
+ * steps of cpm_mlp_train_step, cycling over the fields with
+ * max(1, steps / n_fields) consecutive steps per field, at a learning rate
+ * falling linearly from opts->lr to opts->lr_final.  report (may be NULL):
+ * mean loss over the fields before and after.  Synchronous.
+ * Errors: CPM_ERR_ARG (NULL or empty set, a field of a 2-D hierarchy,
+ * non-finite or zero field).
+ */
+cpm_status cpm_mlp_train(cpm_mlp m, const cpm_train_set* set, const cpm_train_opts* opts,
+                         cpm_train_report* report, cpm_stream stream);
+
+/*
+ * Write the network (parameters, Adam moments and step count) to a file at
+ * path: the 8 bytes "CPMMLP01", int32 CPM_MLP_NPARAMS, int64 step, then
+ * params, m and v as CPM_MLP_NPARAMS little-endian floats each.  Synchronous.
+ */
+cpm_status cpm_mlp_save(cpm_mlp m, const char* path);
+
+/* Create a network from a file written by cpm_mlp_save (CPM_ERR_ARG if the
+ * file is missing, short or of another format).  Synchronous. */
+cpm_status cpm_mlp_load(const char* path, cpm_mlp* out);
+
+
 typedef enum cpm_solve_mode {
   CPM_SOLVE_F64 = 0,   /* FP64 V-cycles in FP64 defect correction            */
   CPM_SOLVE_MIXED = 1  /* FP32 V-cycle preconditioning an FP64 outer loop:
@@ -277,6 +378,13 @@ typedef struct cpm_solve_opts {
                           with the network whose reduction factor exceeds
                           1.25 x the reference switches the network off for
                           the rest of the solve                             */
+  int32_t fmg;         /* 1: the first outer iteration's correction is full
+                          multigrid (remark at Algorithm 4.1): the residual is
+                          restricted to every level, the coarsest level solved,
+                          and on each finer level the prolonged coarse
+                          solution starts one cycle of that level; later
+                          iterations use cycles from zero.  Plain launches for
+                          that iteration; not in batches                    */
 } cpm_solve_opts;
 
 #define CPM_MAX_HISTORY 256

@@ -32,7 +32,7 @@ from dataclasses import dataclass
 
 import numpy as np
 
-from .geometry import ELLIPSOID, Surface, closest_point
+from .geometry import DZIUK, ELLIPSOID, Surface, closest_point
 
 
 def default_lambda2(dim: int, p: int = 3) -> float:
@@ -140,6 +140,16 @@ def _candidate_filter(surface: Surface, X: np.ndarray, reach: float) -> np.ndarr
         a = np.asarray(surface.params)
         rho = np.sqrt(((X / a[None, :]) ** 2).sum(axis=1))
         return a.min() * np.abs(rho - 1.0) <= reach
+    if surface.kind == DZIUK:
+        # first-order distance |phi| / |grad phi|, with a factor 4 of slack for
+        # the curvature (at most about 10.4) over the band half-widths used
+        x1, x2, x3 = X[:, 0], X[:, 1], X[:, 2]
+        a = x1 - x3 * x3
+        phi = a * a + x2 * x2 + x3 * x3 - 1.0
+        g = 2.0 * np.sqrt(a * a + x2 * x2 + (x3 * (1.0 - 2.0 * a)) ** 2)
+        with np.errstate(divide="ignore", invalid="ignore"):
+            est = np.abs(phi) / g
+        return ~(est > 4.0 * reach)
     return np.ones(X.shape[0], dtype=bool)
 
 

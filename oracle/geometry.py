@@ -43,7 +43,12 @@ from dataclasses import dataclass, field
 
 import numpy as np
 
-CIRCLE, SPHERE, TORUS, ELLIPSOID = "circle", "sphere", "torus", "ellipsoid"
+CIRCLE, SPHERE, TORUS, ELLIPSOID, DZIUK = "circle", "sphere", "torus", "ellipsoid", "dziuk"
+
+# Smallest radius of curvature of the Dziuk surface (x1 - x3^2)^2 + x2^2 + x3^2 = 1,
+# 1 / 10.44 near x3 = +-0.92, from the principal curvatures on a fine parameter
+# grid of the surface (``dziuk_min_curvature_radius``, pinned by a test).
+DZIUK_REACH = 0.0957
 
 
 @dataclass(frozen=True)
@@ -68,6 +73,8 @@ class Surface:
         if self.kind == ELLIPSOID:
             a = sorted(self.params)
             return float(a[0] ** 2 / a[-1])
+        if self.kind == DZIUK:
+            return DZIUK_REACH
         raise ValueError(self.kind)
 
 
@@ -85,6 +92,11 @@ def torus(R: float, r: float) -> Surface:
 
 def ellipsoid(a0: float, a1: float, a2: float) -> Surface:
     return Surface(ELLIPSOID, (float(a0), float(a1), float(a2)))
+
+
+def dziuk() -> Surface:
+    """The level set (x1 - x3^2)^2 + x2^2 + x3^2 = 1 of Sec. 4.5.5."""
+    return Surface(DZIUK, ())
 
 
 def _round_sphere(X: np.ndarray, R: float):
@@ -164,6 +176,91 @@ def _ellipsoid(X: np.ndarray, axes):
     return cp, dist2
 
 
+DZIUK_NEWTON_STEPS = 30
+
+
+def _dziuk(X: np.ndarray):
+    """Closest point on phi(y) = (y1 - y3^2)^2 + y2^2 + y3^2 - 1 = 0 by Newton's
+    method on the Lagrange conditions (Sec. 4.5.5 minimises the squared
+    distance with Newton's method):
+
+        y - x + lam g(y) = 0,  phi(y) = 0,   g = grad(phi) / 2
+                                              = (a, y2, y3 (1 - 2a)),  a = y1 - y3^2.
+
+    Start y = x, lam = 0 (the first step is the gradient projection of x);
+    each step solves [K, g; 2 g^T, 0] [dy; dl] = -[F1; F2] with
+    K = I + lam dg/dy, whose only off-diagonal entry is K13 = K31 = -2 lam y3:
+    dl = (F2 - 2 g.K^-1 F1) / (2 g.K^-1 g), dy = -K^-1 (F1 + g dl), K^-1 by
+    the 2x2 block (y1, y3) and the scalar y2 block.  A fixed number of steps,
+    every operation rounded separately in this order (the CUDA path repeats
+    it bit for bit).  Nodes where a step is singular get nan (not in any band).
+    """
+    x1, x2, x3 = X[:, 0].copy(), X[:, 1].copy(), X[:, 2].copy()
+    y1, y2, y3 = x1.copy(), x2.copy(), x3.copy()
+    lam = np.zeros_like(x1)
+    with np.errstate(divide="ignore", invalid="ignore", over="ignore"):
+        for _ in range(DZIUK_NEWTON_STEPS):
+            y3s = y3 * y3
+            a = y1 - y3s
+            g1 = a
+            g2 = y2
+            g3 = y3 * (1.0 - 2.0 * a)
+            F11 = (y1 - x1) + lam * g1
+            F12 = (y2 - x2) + lam * g2
+            F13 = (y3 - x3) + lam * g3
+            F2 = ((a * a + y2 * y2) + y3s) - 1.0
+            k11 = 1.0 + lam
+            k22 = 1.0 + lam
+            k13 = -2.0 * (lam * y3)
+            k33 = 1.0 + lam * ((1.0 - 2.0 * y1) + 6.0 * y3s)
+            det = k11 * k33 - k13 * k13
+            # K^-1 F1 and K^-1 g
+            p1 = (k33 * F11 - k13 * F13) / det
+            p2 = F12 / k22
+            p3 = (k11 * F13 - k13 * F11) / det
+            q1 = (k33 * g1 - k13 * g3) / det
+            q2 = g2 / k22
+            q3 = (k11 * g3 - k13 * g1) / det
+            gp = (g1 * p1 + g2 * p2) + g3 * p3
+            gq = (g1 * q1 + g2 * q2) + g3 * q3
+            dl = (F2 - 2.0 * gp) / (2.0 * gq)
+            y1 = y1 - (p1 + q1 * dl)
+            y2 = y2 - (p2 + q2 * dl)
+            y3 = y3 - (p3 + q3 * dl)
+            lam = lam + dl
+        d1, d2, d3 = x1 - y1, x2 - y2, x3 - y3
+        dist2 = (d1 * d1 + d2 * d2) + d3 * d3
+    cp = np.stack([y1, y2, y3], axis=1)
+    bad = ~np.isfinite(dist2)
+    dist2[bad] = np.inf
+    cp[bad] = np.nan
+    return cp, dist2
+
+
+def dziuk_min_curvature_radius(n: int = 400) -> float:
+    """1 / max |kappa| over the Dziuk surface, from the shape operator
+    (I - n n^T) Hess(phi) (I - n n^T) / |grad phi| at points of the surface
+    x1 = x3^2 + rho cos(t), x2 = rho sin(t), rho = sqrt(1 - x3^2)."""
+    z = np.linspace(-1.0, 1.0, n)[1:-1]
+    t = np.linspace(0.0, 2 * np.pi, 2 * n, endpoint=False)
+    Z, T = np.meshgrid(z, t, indexing="ij")
+    rho = np.sqrt(1.0 - Z * Z)
+    P = np.stack([Z * Z + rho * np.cos(T), rho * np.sin(T), Z], axis=-1).reshape(-1, 3)
+    a = P[:, 0] - P[:, 2] ** 2
+    G = 2.0 * np.stack([a, P[:, 1], P[:, 2] * (1.0 - 2.0 * a)], axis=1)
+    H = np.zeros((len(P), 3, 3))
+    H[:, 0, 0] = 2.0
+    H[:, 1, 1] = 2.0
+    H[:, 0, 2] = H[:, 2, 0] = -4.0 * P[:, 2]
+    H[:, 2, 2] = 2.0 - 4.0 * a + 8.0 * P[:, 2] ** 2
+    g = np.linalg.norm(G, axis=1)
+    nrm = G / g[:, None]
+    Pr = np.eye(3)[None] - nrm[:, :, None] * nrm[:, None, :]
+    S = Pr @ H @ Pr / g[:, None, None]
+    kmax = np.abs(np.linalg.eigvalsh(S)).max()
+    return float(1.0 / kmax)
+
+
 def closest_point(surface: Surface, X: np.ndarray):
     """(cp, dist2) of the grid nodes X, shape (N, d), float64."""
     X = np.asarray(X, dtype=np.float64)
@@ -173,4 +270,6 @@ def closest_point(surface: Surface, X: np.ndarray):
         return _torus(X, *surface.params)
     if surface.kind == ELLIPSOID:
         return _ellipsoid(X, surface.params)
+    if surface.kind == DZIUK:
+        return _dziuk(X)
     raise ValueError(surface.kind)

@@ -47,7 +47,7 @@ import scipy.linalg as sla
 from .band import Band, build_band
 from .geometry import Surface
 from .interp import interp_matrix
-from .operators import Operators
+from .operators import Operators, PaperOperators, VarDiffOperators
 
 
 @dataclass
@@ -65,11 +65,16 @@ class MGOptions:
     nu1: int = 2
     nu2: int = 2
     omega: float = 2.0 / 3.0
-    smoother: str = "rm"              # "rm" | "jacobi"
+    smoother: str = "rm"              # "rm" | "jacobi" | "rbgs" (red-black Gauss-Seidel on A)
     transfer_p: int = 1
     p: int = 3
     residual: str = "extended"        # "extended": f - A(E u) (Sec. 4.4); "plain": f - A u
     coarse_sweeps: int = 0            # > 0: coarsest level by Jacobi sweeps instead of LU
+    operator: str = "mbr"             # "mbr": diag(L) + (L - diag L) E (Eq. 2.10);
+                                      # "paper": E_1 L_band - gamma (I - E_3) (Eq. 3.3)
+    cycle: int = 1                    # coarse-grid corrections per level: 1 V-cycle, 2 W-cycle
+    # operator "vardiff": E_3 L~ - gamma (I - E_3) with L~ the variable-diffusion
+    # Laplacian of Sec. 4.5.6; a_fn(cp) gives the coefficient on the finest band
 
 
 @dataclass
@@ -89,19 +94,21 @@ def coarsest_spacing_ok(surface: Surface, dx: float, lambda2: float) -> bool:
 
 
 def build_hierarchy(surface: Surface, dx: float, coarsest_dx: float, c=1.0,
-                    opts: MGOptions | None = None, c_fn=None) -> Hierarchy:
+                    opts: MGOptions | None = None, c_fn=None, a_fn=None) -> Hierarchy:
     """Levels dx, 2dx, .., coarsest_dx.  ``c_fn(cp) -> c`` gives a variable c.
 
     A variable c is c_fn(cp(x)) on the finest band; coarser levels carry the
     restriction of the finer level's c (linear interpolation at their closest
-    points), the reading that needs c only on the finest band.
+    points), the reading that needs c only on the finest band.  The diffusion
+    coefficient a of the "vardiff" operator (a_fn) is carried the same way.
     """
     opts = opts or MGOptions()
     levels = []
     h = dx
     while True:
         band = build_band(surface, h, p=opts.p)
-        ops = Operators(band, opts.p)
+        ops = (PaperOperators(band, opts.p) if opts.operator == "paper"
+               else None if opts.operator == "vardiff" else Operators(band, opts.p))
         levels.append(Level(band, ops, np.full(band.nb, float(c))))
         if h >= coarsest_dx * (1 - 1e-12):
             break
@@ -110,6 +117,12 @@ def build_hierarchy(surface: Surface, dx: float, coarsest_dx: float, c=1.0,
         fine, coarse = levels[l], levels[l + 1]
         fine.R = interp_matrix(fine.band, coarse.band.cp[: coarse.band.nb], opts.transfer_p)
         fine.P = interp_matrix(coarse.band, fine.band.cp[: fine.band.nb], opts.transfer_p)
+    if opts.operator == "vardiff":
+        a = np.asarray(a_fn(levels[0].band.cp[: levels[0].band.nb]), dtype=np.float64)
+        for l, lev in enumerate(levels):
+            if l > 0:
+                a = levels[l - 1].R @ a
+            lev.ops = VarDiffOperators(lev.band, a, opts.p)
     if c_fn is not None:
         # c is a surface function (footnote to Sec. 2.1) known on the finest band
         # as c(cp(x)); each coarser level takes it at its own closest points by
@@ -126,8 +139,22 @@ def build_hierarchy(surface: Surface, dx: float, coarsest_dx: float, c=1.0,
     return hier
 
 
+def colour(band) -> np.ndarray:
+    """Red (0) / black (1) colour of the band nodes: parity of i + j (+ k)."""
+    return band.coords_of(band.keys).sum(axis=1) % 2
+
+
 def smooth(hier: Hierarchy, l: int, u: np.ndarray, f: np.ndarray) -> np.ndarray:
     lev, o = hier.levels[l], hier.opts
+    if o.smoother == "rbgs":
+        # Gauss-Seidel in red-black order (Sec. 4.4 names Gauss-Seidel as an
+        # alternative to Jacobi): the red nodes take the weighted Jacobi update
+        # of the current iterate, then the black nodes that of the updated one.
+        col = colour(lev.band)
+        for c in (0, 1):
+            r = f - lev.ops.apply_A(u, lev.c)
+            u = u + np.where(col == c, o.omega * r / lev.diagA, 0.0)
+        return u
     if o.smoother == "rm":
         u = u + o.omega * (f - lev.ops.apply_Atilde(u, lev.c)) / lev.ops.diag_Atilde(lev.c)
         return lev.ops.extend(u)[: lev.ops.nb]
@@ -170,10 +197,27 @@ def vcycle(hier: Hierarchy, u: np.ndarray, f: np.ndarray, l: int = 0) -> np.ndar
     if l + 1 == len(hier.levels) - 1:
         uc = coarse_solve(hier, fc)
     else:
-        uc = vcycle(hier, np.zeros_like(fc), fc, l + 1)
+        # V-cycle (cycle = 1) or W-cycle (cycle = 2): that many cycles of the
+        # next level, the first from zero (remark at Algorithm 4.1)
+        uc = np.zeros_like(fc)
+        for _ in range(o.cycle):
+            uc = vcycle(hier, uc, fc, l + 1)
     u = u + lev.P @ uc
     for _ in range(o.nu2):
         u = smooth(hier, l, u, f)
+    return u
+
+
+def fmg(hier: Hierarchy, f: np.ndarray) -> np.ndarray:
+    """Full multigrid from zero: f restricted to every level, the coarsest
+    level solved, then on each finer level the prolonged coarse solution is the
+    start of one cycle of that level (remark at Algorithm 4.1)."""
+    fs = [f]
+    for l in range(len(hier.levels) - 1):
+        fs.append(hier.levels[l].R @ fs[-1])
+    u = coarse_solve(hier, fs[-1])
+    for l in range(len(hier.levels) - 2, -1, -1):
+        u = vcycle(hier, hier.levels[l].P @ u, fs[l], l)
     return u
 
 
@@ -185,8 +229,9 @@ class SolveReport:
 
 
 def solve(hier: Hierarchy, f: np.ndarray, tol: float = 1e-10, max_iter: int = 100,
-          u0: np.ndarray | None = None) -> tuple[np.ndarray, SolveReport]:
-    """Outer defect correction: u += V(0, f - A u) until ||r||/||f|| <= tol."""
+          u0: np.ndarray | None = None, first_fmg: bool = False) -> tuple[np.ndarray, SolveReport]:
+    """Outer defect correction: u += V(0, f - A u) until ||r||/||f|| <= tol
+    (first_fmg: the first correction is the full-multigrid solution of f - A u)."""
     fine = hier.fine
     u = np.zeros_like(f) if u0 is None else u0.copy()
     fn = np.abs(f).max()
@@ -199,5 +244,5 @@ def solve(hier: Hierarchy, f: np.ndarray, tol: float = 1e-10, max_iter: int = 10
             return u, SolveReport(it, hist, True)
         if it == max_iter:
             break
-        u = u + vcycle(hier, np.zeros_like(r), r)
+        u = u + (fmg(hier, r) if first_fmg and it == 0 else vcycle(hier, np.zeros_like(r), r))
     return u, SolveReport(max_iter, hist, False)

@@ -146,3 +146,75 @@ def paper_M(band: Band) -> sp.csr_matrix:
     L = lap_band(band)
     g = gamma(band)
     return (E1 @ L - g * (sp.identity(nb, format="csr") - E3)).tocsr()
+
+
+class PaperOperators(Operators):
+    """The paper's scheme (Eq. 3.3) behind the interface of ``Operators``:
+    M = E_1 L_band - gamma (I - E_3) on B, assembled by ``paper_M`` and applied
+    as a sparse product.  E (cubic, rows B+) is kept for the re-extended
+    residual of Sec. 4.4; everything else follows from M."""
+
+    def __init__(self, band: Band, p: int = 3):
+        super().__init__(band, p)
+        self._M = paper_M(band)
+
+    @property
+    def M(self) -> sp.csr_matrix:
+        return self._M
+
+    def apply_M(self, u: np.ndarray) -> np.ndarray:
+        return self._M @ u
+
+    def diag_M(self) -> np.ndarray:
+        return self._M.diagonal().copy()
+
+
+def lap_vardiff(band: Band, a: np.ndarray) -> sp.csr_matrix:
+    """L~ = sum over axes of D^b diag(A^f a) D^f (Sec. 4.5.6) restricted to B:
+    for a band node i and each neighbour k = i +- e_axis in B, the face
+    coefficient (a_i + a_k) / 2 multiplies (u_k - u_i) / dx^2; neighbours
+    outside B are dropped, as in the band-restricted L."""
+    nb = band.nb
+    h2 = band.dx * band.dx
+    nbk = band.neighbour_keys(band.keys)
+    idx = band.index_in_band(nbk.ravel()).reshape(nbk.shape)
+    r, q = np.nonzero(idx >= 0)
+    k = idx[r, q]
+    face = 0.5 * (a[r] + a[k]) / h2
+    rows = np.concatenate([r, r])
+    cols = np.concatenate([k, r])
+    vals = np.concatenate([face, -face])
+    return sp.csr_matrix((vals, (rows, cols)), shape=(nb, nb))
+
+
+class VarDiffOperators(Operators):
+    """Variable diffusion (Sec. 4.5.6): M = E_1 L~ - diag(gamma a) (I - E_3) on B
+    with L~ from ``lap_vardiff`` and a the diffusion coefficient at the closest
+    points of B.  The section writes one E for both terms and one gamma; as in
+    Eq. 3.3 the differential term takes linear (E_1) and the side condition
+    cubic (E_3) interpolation, and the side condition of node i is weighted by
+    gamma a_i, gamma = 2d/dx^2, so that it balances the local diffusion as
+    gamma balances a unit coefficient (with E_3 in both terms, or one gamma,
+    Jacobi-smoothed V-cycles diverge on the sphere at dx = 1/32).  With a = 1
+    this is the paper-form M of Eq. 3.3 exactly."""
+
+    def __init__(self, band: Band, a: np.ndarray, p: int = 3):
+        super().__init__(band, p)
+        nb = band.nb
+        self.a = np.asarray(a, dtype=np.float64)
+        E1 = interp_matrix(band, band.cp[:nb], 1)
+        E3 = interp_matrix(band, band.cp[:nb], p)
+        self.Lt = lap_vardiff(band, self.a)
+        G = sp.diags(self.gamma * self.a)
+        self._M = (E1 @ self.Lt - G @ (sp.identity(nb, format="csr") - E3)).tocsr()
+
+    @property
+    def M(self) -> sp.csr_matrix:
+        return self._M
+
+    def apply_M(self, u: np.ndarray) -> np.ndarray:
+        return self._M @ u
+
+    def diag_M(self) -> np.ndarray:
+        return self._M.diagonal().copy()
+

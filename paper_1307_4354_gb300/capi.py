@@ -15,11 +15,12 @@ from . import _build
 
 CPM_OK, CPM_ERR_ARG, CPM_ERR_OOM, CPM_ERR_CUDA, CPM_ERR_REACH = 0, 1, 2, 3, 4
 CPM_ERR_DIVERGED, CPM_ERR_NOT_CONVERGED, CPM_ERR_TIMEOUT, CPM_ERR_CHECKED, CPM_ERR_SINGULAR = 5, 6, 7, 8, 9
-CPM_CIRCLE, CPM_SPHERE, CPM_TORUS, CPM_ELLIPSOID = 0, 1, 2, 3
-CPM_SMOOTH_JACOBI, CPM_SMOOTH_RM = 0, 1
+CPM_CIRCLE, CPM_SPHERE, CPM_TORUS, CPM_ELLIPSOID, CPM_DZIUK = 0, 1, 2, 3, 4
+CPM_SMOOTH_JACOBI, CPM_SMOOTH_RM, CPM_SMOOTH_RBGS = 0, 1, 2
 CPM_F64, CPM_F32 = 0, 1
 CPM_RESID_EXTENDED, CPM_RESID_PLAIN = 0, 1
 CPM_SOLVE_F64, CPM_SOLVE_MIXED = 0, 1
+CPM_OP_MBR, CPM_OP_PAPER, CPM_OP_VARDIFF = 0, 1, 2
 CPM_MAX_HISTORY = 256
 CPM_NOALLOC_MAX_POINTS = 1048576
 
@@ -37,13 +38,14 @@ class cpm_mg_opts(C.Structure):
                 ("omega", C.c_double), ("smoother", C.c_int32), ("transfer_deg", C.c_int32),
                 ("c", C.c_double), ("c_device", C.c_void_p), ("residual_mode", C.c_int32),
                 ("coarse_sweeps", C.c_int32), ("coarse_f64_max", C.c_int32),
-                ("coarse_dense_max", C.c_int32)]
+                ("coarse_dense_max", C.c_int32), ("op_form", C.c_int32), ("cycle", C.c_int32),
+                ("a_device", C.c_void_p)]
 
 
 class cpm_solve_opts(C.Structure):
     _fields_ = [("tol", C.c_double), ("max_iter", C.c_int32), ("mode", C.c_int32),
                 ("use_graph", C.c_int32), ("zero_init", C.c_int32), ("inner_cycles", C.c_int32),
-                ("learned", C.c_int32)]
+                ("learned", C.c_int32), ("fmg", C.c_int32)]
 
 
 class cpm_solve_report(C.Structure):
@@ -55,6 +57,21 @@ class cpm_solve_report(C.Structure):
 
 
 CPM_MLP_NPARAMS = 6337
+
+
+class cpm_train_set(C.Structure):
+    _fields_ = [("n_fields", C.c_int32), ("hier", C.POINTER(C.c_void_p)),
+                ("r", C.POINTER(C.c_void_p))]
+
+
+class cpm_train_opts(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("lr", C.c_float), ("lr_final", C.c_float),
+                ("reset", C.c_int32)]
+
+
+class cpm_train_report(C.Structure):
+    _fields_ = [("steps", C.c_int32), ("n_fields", C.c_int32), ("loss_first", C.c_double),
+                ("loss_last", C.c_double), ("seconds", C.c_double)]
 
 
 class CpmError(RuntimeError):
@@ -73,6 +90,7 @@ _PROTOS = {
                                  C.POINTER(C.c_void_p)]),
     "cpm_band_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
     "cpm_band_export": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]),
+    "cpm_band_counts": (C.c_int, [C.c_void_p, C.POINTER(C.c_int64), C.c_void_p]),
     "cpm_band_destroy": (C.c_int, [C.c_void_p]),
     "cpm_build_hierarchy": (C.c_int, [C.c_void_p, C.POINTER(cpm_mg_opts), C.c_void_p,
                                       C.POINTER(C.c_void_p)]),
@@ -102,6 +120,10 @@ _PROTOS = {
                                     C.c_void_p]),
     "cpm_mlp_train_step": (C.c_int, [C.c_void_p, C.c_void_p, C.c_float, C.POINTER(C.c_double),
                                      C.c_void_p]),
+    "cpm_mlp_train": (C.c_int, [C.c_void_p, C.POINTER(cpm_train_set), C.POINTER(cpm_train_opts),
+                                C.POINTER(cpm_train_report), C.c_void_p]),
+    "cpm_mlp_save": (C.c_int, [C.c_void_p, C.c_char_p]),
+    "cpm_mlp_load": (C.c_int, [C.c_char_p, C.POINTER(C.c_void_p)]),
     "cpm_build_batch": (C.c_int, [C.POINTER(C.c_void_p), C.c_int32, C.c_int32, C.c_char_p,
                                   C.POINTER(C.c_void_p)]),
     "cpm_solve_batch": (C.c_int, [C.c_void_p, C.POINTER(C.c_void_p), C.POINTER(C.c_void_p),
@@ -164,6 +186,12 @@ def cpm_band_info(band: int):
 def cpm_band_export(band: int, ijk_ptr: int | None, cp_ptr: int | None, base_ptr: int | None):
     _check(lib().cpm_band_export(C.c_void_p(band), C.c_void_p(ijk_ptr), C.c_void_p(cp_ptr),
                                  C.c_void_p(base_ptr)), "cpm_band_export")
+
+
+def cpm_band_counts(band: int, stream: int = 0):
+    out = (C.c_int64 * 4)()
+    _check(lib().cpm_band_counts(C.c_void_p(band), out, C.c_void_p(stream)), "cpm_band_counts")
+    return list(out)
 
 
 def cpm_band_destroy(band: int):
@@ -282,6 +310,33 @@ def cpm_mlp_train_step(h: int, r_ptr: int, lr: float, stream: int = 0, want_loss
                                     C.byref(loss) if want_loss else None, C.c_void_p(stream)),
            "cpm_mlp_train_step")
     return loss.value if want_loss else None
+
+
+def cpm_mlp_train(m: int, hiers: list[int], r_ptrs: list[int], opts: cpm_train_opts,
+                  stream: int = 0) -> cpm_train_report:
+    n = len(hiers)
+    if n != len(r_ptrs):
+        raise ValueError("one hierarchy per field")
+    ts = cpm_train_set()
+    ts.n_fields = n
+    ha = (C.c_void_p * n)(*hiers)
+    ra = (C.c_void_p * n)(*r_ptrs)
+    ts.hier = C.cast(ha, C.POINTER(C.c_void_p))
+    ts.r = C.cast(ra, C.POINTER(C.c_void_p))
+    rep = cpm_train_report()
+    _check(lib().cpm_mlp_train(C.c_void_p(m), C.byref(ts), C.byref(opts), C.byref(rep),
+                               C.c_void_p(stream)), "cpm_mlp_train")
+    return rep
+
+
+def cpm_mlp_save(m: int, path: str):
+    _check(lib().cpm_mlp_save(C.c_void_p(m), path.encode()), "cpm_mlp_save")
+
+
+def cpm_mlp_load(path: str) -> int:
+    out = C.c_void_p()
+    _check(lib().cpm_mlp_load(path.encode(), C.byref(out)), "cpm_mlp_load")
+    return out.value
 
 
 def cpm_build_batch(hiers: list[int], n_rhs: int, tune_cache: str | None = None) -> int:

@@ -44,6 +44,9 @@ double surface_reach(const cpm_surface& s) {
       double b = std::fmax(s.param[0], std::fmax(s.param[1], s.param[2]));
       return a * a / b;
     }
+    // largest principal curvature of the Dziuk surface: 10.44 near x3 = +-0.92
+    // (shape operator of the level set evaluated on a fine grid of the surface)
+    case CPM_DZIUK: return 0.0957;
   }
   return 0.0;
 }
@@ -58,6 +61,55 @@ double surface_reach(const cpm_surface& s) {
 //                  bit, cp_i = (a_i^2 x_i) / (a_i^2 + t); if the function is
 //                  never positive the node is on the medial disk: dist2 = inf.
 __device__ inline double dsub(double a, double b) { return __dadd_rn(a, -b); }
+__device__ inline double dadd(double a, double b) { return __dadd_rn(a, b); }
+__device__ inline double dmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ inline double ddiv(double a, double b) { return __ddiv_rn(a, b); }
+
+// Dziuk surface phi(y) = (y1 - y3^2)^2 + y2^2 + y3^2 - 1 (Sec. 4.5.5): closest
+// point by Newton's method on  y - x + lam g(y) = 0, phi(y) = 0  with
+// g = grad(phi)/2 = (a, y2, y3 (1 - 2a)), a = y1 - y3^2, from y = x, lam = 0;
+// 30 steps, each solving [K, g; 2 g^T, 0][dy; dl] = -[F1; F2] with
+// K = I + lam dg/dy (K13 = K31 = -2 lam y3 its only off-diagonal entry):
+// dl = (F2 - 2 g.K^-1 F1) / (2 g.K^-1 g), dy = -K^-1 (F1 + g dl).
+__device__ void dziuk_cp(double x1, double x2, double x3, double cp[3], double& dist2) {
+  double y1 = x1, y2 = x2, y3 = x3, lam = 0.0;
+  for (int it = 0; it < 30; ++it) {
+    const double y3s = dmul(y3, y3);
+    const double a = dsub(y1, y3s);
+    const double g1 = a, g2 = y2, g3 = dmul(y3, dsub(1.0, dmul(2.0, a)));
+    const double F11 = dadd(dsub(y1, x1), dmul(lam, g1));
+    const double F12 = dadd(dsub(y2, x2), dmul(lam, g2));
+    const double F13 = dadd(dsub(y3, x3), dmul(lam, g3));
+    const double F2 = dsub(dadd(dadd(dmul(a, a), dmul(y2, y2)), y3s), 1.0);
+    const double k11 = dadd(1.0, lam), k22 = dadd(1.0, lam);
+    const double k13 = dmul(-2.0, dmul(lam, y3));
+    const double k33 = dadd(1.0, dmul(lam, dadd(dsub(1.0, dmul(2.0, y1)), dmul(6.0, y3s))));
+    const double det = dsub(dmul(k11, k33), dmul(k13, k13));
+    const double p1 = ddiv(dsub(dmul(k33, F11), dmul(k13, F13)), det);
+    const double p2 = ddiv(F12, k22);
+    const double p3 = ddiv(dsub(dmul(k11, F13), dmul(k13, F11)), det);
+    const double q1 = ddiv(dsub(dmul(k33, g1), dmul(k13, g3)), det);
+    const double q2 = ddiv(g2, k22);
+    const double q3 = ddiv(dsub(dmul(k11, g3), dmul(k13, g1)), det);
+    const double gp = dadd(dadd(dmul(g1, p1), dmul(g2, p2)), dmul(g3, p3));
+    const double gq = dadd(dadd(dmul(g1, q1), dmul(g2, q2)), dmul(g3, q3));
+    const double dl = ddiv(dsub(F2, dmul(2.0, gp)), dmul(2.0, gq));
+    y1 = dsub(y1, dadd(p1, dmul(q1, dl)));
+    y2 = dsub(y2, dadd(p2, dmul(q2, dl)));
+    y3 = dsub(y3, dadd(p3, dmul(q3, dl)));
+    lam = dadd(lam, dl);
+  }
+  const double d1 = dsub(x1, y1), d2 = dsub(x2, y2), d3 = dsub(x3, y3);
+  dist2 = dadd(dadd(dmul(d1, d1), dmul(d2, d2)), dmul(d3, d3));
+  if (!isfinite(dist2)) {
+    cp[0] = cp[1] = cp[2] = CUDART_NAN;
+    dist2 = CUDART_INF;
+    return;
+  }
+  cp[0] = y1;
+  cp[1] = y2;
+  cp[2] = y3;
+}
 
 __device__ void closest_point_f64(const SurfaceDev& s, double x, double y, double z, double cp[3],
                                   double& dist2) {
@@ -85,6 +137,8 @@ __device__ void closest_point_f64(const SurfaceDev& s, double x, double y, doubl
     cp[0] = __dmul_rn(x, k);
     cp[1] = __dmul_rn(y, k);
     cp[2] = __dmul_rn(z, sc);
+  } else if (s.kind == CPM_DZIUK) {
+    dziuk_cp(x, y, z, cp, dist2);
   } else {  // ellipsoid
     const double X[3] = {x, y, z};
     double a2[3], ax[3];
@@ -134,6 +188,15 @@ __device__ inline float dist_lower_f32(const SurfaceDev& s, float x, float y, fl
   if (s.kind == CPM_TORUS) {
     const float a = sqrtf(x * x + y * y) - (float)s.p[0];
     return fabsf(sqrtf(a * a + z * z) - (float)s.p[1]);
+  }
+  if (s.kind == CPM_DZIUK) {
+    // first-order distance |phi| / |grad phi| with a factor 4 of slack for the
+    // curvature (at most 10.44) over the band half-widths the reach allows
+    const float a = x - z * z;
+    const float phi = a * a + y * y + z * z - 1.0f;
+    const float b = z * (1.0f - 2.0f * a);
+    const float g = 2.0f * sqrtf(a * a + y * y + b * b);
+    return g > 0.f ? 0.25f * fabsf(phi) / g : 1e30f;
   }
   // ellipsoid: |x - y| >= a_min |rho - 1| for every y on S, rho = |D^-1 x|
   const float a0 = (float)s.p[0], a1 = (float)s.p[1], a2 = (float)s.p[2];
@@ -474,6 +537,71 @@ __global__ void k_neighbours(BrickView v, const uint64_t* key, int32_t nB, int d
   }
 }
 
+// 9. Brick records: masks and starts of every occupied brick and of its face
+// neighbours (order -x, +x, -y, +y, -z, +z).
+__global__ void k_brick_recs(BrickView v, const uint32_t* bcoord, int dim, BrickRec* rec) {
+  const int32_t b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= v.nbricks) return;
+  const uint32_t c = bcoord[b];
+  const int bx = (int)(c & 1023), by = (int)((c >> 10) & 1023), bz = (int)((c >> 20) & 1023);
+  const int d[7][3] = {{0, 0, 0}, {-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  BrickRec r;
+  for (int q = 0; q < 7; ++q) {
+    const int x = bx + d[q][0], y = by + d[q][1], z = bz + d[q][2];
+    int32_t nb = -1;
+    if (q <= 2 * dim && x >= 0 && y >= 0 && z >= 0 && x < v.nbx && y < v.nby && z < v.nbz)
+      nb = v.map[((size_t)z * v.nby + y) * v.nbx + x];
+    r.bm[q] = nb >= 0 ? v.bmask[nb] : 0ull;
+    r.gm[q] = nb >= 0 ? v.gmask[nb] : 0ull;
+    r.bs[q] = nb >= 0 ? v.bstart[nb] : 0;
+    r.gs[q] = nb >= 0 ? v.gstart[nb] : 0;
+  }
+  rec[b] = r;
+}
+
+// 10. Table 4.1 counts: per band point the number of its 2d Laplacian
+// neighbours inside B (the band-restricted L) and whether the node lies outside
+// its own cubic stencil (an extra diagonal entry of M = E_1 L - gamma (I - E_3)).
+__global__ void k_band_counts(BrickView v, const uint64_t* key, int32_t nB, int dim,
+                              unsigned long long* acc) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  unsigned long long nl = 0, outside = 0;
+  if (i < nB) {
+    const uint64_t k = key[i];
+    const int x = key_x(k), y = key_y(k), z = key_z(k);
+    const int d[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+    for (int q = 0; q < 2 * dim; ++q)
+      nl += band_index(v, x + d[q][0], y + d[q][1], z + d[q][2]) >= 0;
+    const int off[3] = {-key_ox(k), -key_oy(k), dim == 3 ? -key_oz(k) : 0};
+    for (int a = 0; a < dim; ++a) outside |= (off[a] < 0 || off[a] > 3);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    nl += __shfl_xor_sync(0xffffffffu, nl, o);
+    outside += __shfl_xor_sync(0xffffffffu, outside, o);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicAdd(acc, nl);
+    atomicAdd(acc + 1, outside);
+  }
+}
+
+void band_counts(const Level& L, cudaStream_t st, int64_t counts[4]) {
+  DBuf<unsigned long long> acc(2);
+  CPM_CUDA_TRY(cudaMemsetAsync(acc.get(), 0, 2 * sizeof(unsigned long long), st));
+  if (L.nB > 0)
+    k_band_counts<<<(unsigned)((L.nB + 255) / 256), 256, 0, st>>>(L.view(), L.key.get(), L.nB, L.dim,
+                                                                   acc.get());
+  CPM_CUDA_TRY(cudaGetLastError());
+  unsigned long long h[2];
+  CPM_CUDA_TRY(cudaMemcpyAsync(h, acc.get(), sizeof(h), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  const int64_t nE = (int64_t)L.nB * (L.dim == 3 ? 64 : 16);
+  counts[0] = L.nB;
+  counts[1] = L.nB + (int64_t)h[0];
+  counts[2] = nE;
+  counts[3] = nE + (int64_t)h[1];
+}
+
 // ----------------------------------------------------------------- driver
 static unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
@@ -563,6 +691,9 @@ void build_level(const cpm_surface& surf, double lo, double dx, int n, double la
   L.gstart.alloc(nocc);
   k_copy_i64_to_i32<<<blocks_for(nocc, 256), 256, 0, st>>>(bcount.get(), L.bstart.get(), nocc);
   k_copy_i64_to_i32<<<blocks_for(nocc, 256), 256, 0, st>>>(gcount.get(), L.gstart.get(), nocc);
+  L.brec.alloc(nocc);
+  k_brick_recs<<<blocks_for(nocc, 256), 256, 0, st>>>(L.view(), L.bcoord.get(), dim, L.brec.get());
+  CPM_CUDA_TRY(cudaGetLastError());
 
   // 6. points
   const int64_t np = nB + nG;

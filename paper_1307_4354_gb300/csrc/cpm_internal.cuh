@@ -91,6 +91,16 @@ __host__ __device__ inline int key_ox(uint64_t k) { return (int)((k >> 48) & 15u
 __host__ __device__ inline int key_oy(uint64_t k) { return (int)((k >> 52) & 15u) - 8; }
 __host__ __device__ inline int key_oz(uint64_t k) { return (int)((k >> 56) & 15u) - 8; }
 
+// ----------------------------------------------------------------- brick records
+// Per brick, the occupancy masks and starts of the brick itself (slot 0) and
+// of its face neighbours (slots 1..6: -x, +x, -y, +y, -z, +z; zero masks where
+// there is none), so that a stencil pass finds every Laplacian neighbour with
+// loads addressed by the brick number alone.
+struct BrickRec {
+  uint64_t bm[7], gm[7];
+  int32_t bs[7], gs[7];
+};
+
 // ----------------------------------------------------------------- brick view
 // Plain-pointer view of a level's brick tables, passed by value to kernels.
 struct BrickView {
@@ -99,9 +109,11 @@ struct BrickView {
   const uint64_t* gmask;  // ghost occupancy
   const int32_t* bstart;  // first band index of the brick
   const int32_t* gstart;  // first ghost index of the brick (relative to nB)
+  const BrickRec* brec;   // nbricks brick records
   int nbx, nby, nbz;
   int n;                  // nodes per axis
   int32_t nB;
+  int32_t nbricks;
 };
 
 // Index in B+ of grid node (x, y, z) (B: [0, nB), G: [nB, nB+nG)), or -1.
@@ -147,6 +159,7 @@ struct Level {
   DBuf<uint64_t> bmask, gmask;
   DBuf<int32_t> bstart, gstart;
   DBuf<uint32_t> bcoord;  // packed brick coordinates bx | by << 10 | bz << 20 (<= 1023 each)
+  DBuf<BrickRec> brec;    // per brick: masks and starts of it and its face neighbours
   // per point of B+
   DBuf<uint64_t> key;
   DBuf<double> cp;    // d x (nB+nG), SoA
@@ -164,13 +177,20 @@ struct Level {
   DBuf<uint32_t> erec;        // band index << 6 | stencil base inside the brick
   DBuf<float> efr32;          // d x (nB+nG) fractions in E order
   DBuf<double> ew64;          // 4d x (nB+nG) FP64 cubic weights in E order
+  // chunks: runs of at most kChunkMax consecutive E-order points of one tile
+  // that share one stencil base (and are all in B or all in G); one thread
+  // loads the base's 4^d values once and evaluates every point of the chunk
+  int32_t nchunks = 0;
+  DBuf<uint32_t> echunk;      // first E-order point | (count - 1) << 26
+  DBuf<int32_t> tile_cstart;  // ntiles + 1 offsets into echunk
+  DBuf<int32_t> tile_cmid;    // per tile: end of its chunks of points of B
   DBuf<int32_t> nbr;          // 2d x nB: B+ index of the Laplacian neighbours of B
 
   BrickView view() const {
     BrickView v;
     v.map = map.get(); v.bmask = bmask.get(); v.gmask = gmask.get();
-    v.bstart = bstart.get(); v.gstart = gstart.get();
-    v.nbx = nbx; v.nby = nby; v.nbz = nbz; v.n = n; v.nB = nB;
+    v.bstart = bstart.get(); v.gstart = gstart.get(); v.brec = brec.get();
+    v.nbx = nbx; v.nby = nby; v.nbz = nbz; v.n = n; v.nB = nB; v.nbricks = nbricks;
     return v;
   }
   int64_t nplus() const { return (int64_t)nB + nG; }
@@ -179,6 +199,8 @@ struct Level {
 // Build the band of one level (band.cu).  Throws cpm::Error.
 void build_level(const cpm_surface& s, double lo, double dx, int n, double lambda2,
                  cudaStream_t st, Level& out);
+// |B|, nnz(L_B), nnz(E_3), nnz(E_1 L_B - gamma (I - E_3)) of a level (band.cu).
+void band_counts(const Level& L, cudaStream_t st, int64_t counts[4]);
 // Group the points of a level into extension tiles (ext.cu).
 void build_ext_tiles(Level& L, cudaStream_t st);
 

@@ -22,8 +22,8 @@ static unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 // For each target point (its cp), the base node floor((cp - lo)/dx_src) of the
 // linear stencil in the source grid and the fractions; every stencil node
 // must be a band node of the source level.
-__global__ void k_transfer_records(const double* cp, int64_t cp_stride, int32_t n, int dim,
-                                   double lo, double dx, BrickView src, int32_t* src_idx,
+__global__ void k_transfer_records(const double* cp, int64_t cp_stride, int32_t n, int dim, int deg,
+                                   double lo, double dx, BrickView src, uint64_t* base,
                                    double* fr64, float* fr32, int32_t* err) {
   const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
@@ -32,17 +32,18 @@ __global__ void k_transfer_records(const double* cp, int64_t cp_stride, int32_t 
     const double t = __ddiv_rn(__dadd_rn(cp[a * cp_stride + j], -lo), dx);
     const double fl = floor(t);
     const double s = __dadd_rn(t, -fl);
-    b[a] = (int)fl;
+    b[a] = (int)fl - (deg == 3 ? 1 : 0);
     fr64[(int64_t)a * n + j] = s;
     fr32[(int64_t)a * n + j] = (float)s;
   }
-  for (int c = 0; c < (dim == 3 ? 2 : 1); ++c)
-    for (int bb = 0; bb < 2; ++bb)
-      for (int a = 0; a < 2; ++a) {
-        const int32_t idx = band_index(src, b[0] + a, b[1] + bb, b[2] + c);
-        if (idx < 0) atomicOr(err, 4);
-        src_idx[(int64_t)(4 * c + 2 * bb + a) * n + j] = idx < 0 ? 0 : idx;
-      }
+  bool ok = b[0] >= 0 && b[1] >= 0 && b[2] >= 0;
+  const int np1 = deg + 1;
+  for (int c = 0; c < (dim == 3 ? np1 : 1); ++c)
+    for (int bb = 0; bb < np1; ++bb)
+      for (int a = 0; a < np1; ++a)
+        if (band_index(src, b[0] + a, b[1] + bb, b[2] + c) < 0) ok = false;
+  if (!ok) atomicOr(err, 4);
+  base[j] = ok ? ((uint64_t)b[0] | ((uint64_t)b[1] << 16) | ((uint64_t)b[2] << 32)) : 0ull;
 }
 
 // dA = c - diag(M) in FP64 and FP32.
@@ -56,8 +57,30 @@ __global__ void k_diag_A(const double* diagM, const double* cvec, double cval, d
   dA32[i] = (float)v;
 }
 
+// Linear transfers read their 2^d source indices from a per-target table (1)
+// or find them through the source brick tables (0).
+#ifndef CPM_TRANSFER_INDEXED
+#define CPM_TRANSFER_INDEXED 1
+#endif
+
+__global__ void k_transfer_index(const uint64_t* base, int32_t n, int dim, BrickView src, int32_t* idx) {
+  const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const uint64_t kb = base[j];
+  const int x = (int)(kb & 0xffffu), y = (int)((kb >> 16) & 0xffffu), z = (int)((kb >> 32) & 0xffffu);
+  for (int c = 0; c < (dim == 3 ? 2 : 1); ++c)
+    for (int bb = 0; bb < 2; ++bb)
+      for (int a = 0; a < 2; ++a) {
+        const int32_t i = band_index(src, x + a, y + bb, z + c);
+        idx[(int64_t)(4 * c + 2 * bb + a) * n + j] = i < 0 ? 0 : i;
+      }
+}
+
 struct Transfer {
-  DBuf<int32_t> src_idx;
+  DBuf<uint64_t> base;
+  DBuf<int32_t> idx;  // linear, indexed: 2^d x n source indices
+  BrickView src{};
+  int deg = 1;
   DBuf<double> fr64;
   DBuf<float> fr32;
   int32_t n = 0;
@@ -65,13 +88,14 @@ struct Transfer {
 
 template <typename T>
 struct Work {
-  DBuf<T> u, f, r, w, tmp;
-  void alloc(int64_t nB, int64_t nplus) {
+  DBuf<T> u, f, r, w, tmp, v;
+  void alloc(int64_t nB, int64_t nplus, bool paper) {
     u.alloc(nB);
     f.alloc(nB);
     r.alloc(nB);
     w.alloc(nplus);
     tmp.alloc(nB);
+    if (paper) v.alloc(nB);  // L_B u of the paper-form operator
   }
 };
 
@@ -79,6 +103,8 @@ struct HLevel {
   std::unique_ptr<Level> lev;
   DBuf<double> c64;   // per-point c (empty: scalar)
   DBuf<float> c32;
+  DBuf<double> a64;   // diffusion coefficient (CPM_OP_VARDIFF)
+  DBuf<float> a32;
   DBuf<double> dA64;  // omega / (c - diag(M))
   DBuf<float> dA32;
   DBuf<double> dM64;  // diag(M)
@@ -114,6 +140,9 @@ LevelView<double> HLevel::view<double>() const {
   v.efr = lev->efr32.get();
   v.ew64 = lev->ew64.get();
   v.ntiles = lev->ntiles;
+  v.echunk = lev->echunk.get();
+  v.tile_cstart = lev->tile_cstart.get();
+  v.tile_cmid = lev->tile_cmid.get();
   v.nbr = lev->nbr.get();
   return v;
 }
@@ -138,11 +167,17 @@ LevelView<float> HLevel::view<float>() const {
   v.efr = lev->efr32.get();
   v.ew64 = lev->ew64.get();
   v.ntiles = lev->ntiles;
+  v.echunk = lev->echunk.get();
+  v.tile_cstart = lev->tile_cstart.get();
+  v.tile_cmid = lev->tile_cmid.get();
   v.nbr = lev->nbr.get();
   return v;
 }
 template <> const double* HLevel::cvec<double>() const { return c64.get(); }
 template <> const float* HLevel::cvec<float>() const { return c32.get(); }
+template <typename T> static const T* avec_of(const HLevel& lv);
+template <> const double* avec_of<double>(const HLevel& lv) { return lv.a64.get(); }
+template <> const float* avec_of<float>(const HLevel& lv) { return lv.a32.get(); }
 template <> const double* HLevel::dA<double>() const { return dA64.get(); }
 template <> const float* HLevel::dA<float>() const { return dA32.get(); }
 
@@ -150,11 +185,11 @@ template <typename T>
 static TransferView<T> tview(const Transfer& t, int dim);
 template <>
 TransferView<double> tview<double>(const Transfer& t, int dim) {
-  return TransferView<double>{t.src_idx.get(), t.fr64.get(), t.n, dim};
+  return TransferView<double>{t.base.get(), t.fr64.get(), t.src, t.n, dim, t.deg, t.idx.get()};
 }
 template <>
 TransferView<float> tview<float>(const Transfer& t, int dim) {
-  return TransferView<float>{t.src_idx.get(), t.fr32.get(), t.n, dim};
+  return TransferView<float>{t.base.get(), t.fr32.get(), t.src, t.n, dim, t.deg, t.idx.get()};
 }
 
 }  // namespace cpm
@@ -218,11 +253,14 @@ static void alloc_workspace(const cpm_hier_s& H, Workspace& W, double* norms_slo
   W.w32.resize(H.L.size());
   for (size_t l = 0; l < H.L.size(); ++l) {
     const int64_t nB = H.L[l].lev->nB, np = H.L[l].lev->nplus();
-    W.w64[l].alloc(nB, np);
-    W.w32[l].alloc(nB, np);
+    const bool paper = H.opts.op_form != CPM_OP_MBR;
+    W.w64[l].alloc(nB, np, paper);
+    W.w32[l].alloc(nB, np, paper);
   }
   const int64_t nB0 = H.L[0].lev->nB;
-  W.part_blocks = (int)std::max<int64_t>(nblk(nB0, 256), kNormBlocks);
+  W.part_blocks = std::max<int>(std::max(lap_blocks_f64(H.L[0].view<double>()),
+                                          paper_blocks(H.L[0].view<double>())),
+                                 kNormBlocks);
   W.part.alloc(2 * (size_t)W.part_blocks);
   W.own_norms.alloc(4);
   W.norms = norms_slot ? norms_slot : W.own_norms.get();
@@ -243,6 +281,36 @@ static void alloc_workspace(const cpm_hier_s& H, Workspace& W, double* norms_slo
 namespace cpm {
 
 // ----------------------------------------------------------------- level ops
+// The operator of level l in the hierarchy's form: M u (APPLY), the residual
+// f - A u (RESID, block partials into part when given) or one weighted Jacobi
+// sweep on A u = f in place (JACOBI).  MBR form: w = E u on B+, then the
+// stencil on w; paper form: v = L_B u and w = E_3 u on B, then E_1 v - gamma
+// (u - w).
+template <typename T>
+static void level_op(cpm_hier_s* H, Workspace& W, int l, LapMode mode, const T* f, const T* u,
+                     T* out, double* part, cudaStream_t st) {
+  HLevel& lv = H->L[l];
+  const LevelView<T> v = lv.view<T>();
+  Work<T>& w = W.work<T>(l);
+  const bool upd = mode == LAP_JACOBI || mode == LAP_JAC_RED || mode == LAP_JAC_BLACK;
+  const T* dA = upd ? lv.dA<T>() : nullptr;
+  T* u_inout = upd ? const_cast<T*>(u) : nullptr;
+  if (H->opts.op_form == CPM_OP_PAPER || H->opts.op_form == CPM_OP_VARDIFF) {
+    const T* a = H->opts.op_form == CPM_OP_VARDIFF ? avec_of<T>(lv) : nullptr;
+    if (a)
+      launch_lap_vard<T>(v, u, a, w.v.get(), st);
+    else
+      launch_lap_band<T>(v, u, w.v.get(), st);
+    launch_extend<T>(v, u, w.w.get(), v.nB, st);
+    launch_paper<T>(v, mode, u, w.v.get(), w.w.get(), f, lv.cvec<T>(), (T)H->c, dA, out, u_inout,
+                    part, a, st);
+  } else {
+    launch_extend<T>(v, u, w.w.get(), (int32_t)v.nplus, st);
+    launch_lap<T>(v, mode, u, w.w.get(), f, lv.cvec<T>(), (T)H->c, dA, (T)H->opts.omega, out,
+                  u_inout, part, 0, st);
+  }
+}
+
 template <typename T>
 static void smooth(cpm_hier_s* H, Workspace& W, int l, const T* f, T* u, int sweeps,
                    cudaStream_t st) {
@@ -255,10 +323,11 @@ static void smooth(cpm_hier_s* H, Workspace& W, int l, const T* f, T* u, int swe
     if (H->opts.smoother == CPM_SMOOTH_RM) {
       launch_rm_jacobi<T>(v, u, f, lv.cvec<T>(), cval, omega, w.tmp.get(), st);
       launch_extend<T>(v, w.tmp.get(), u, v.nB, st);
+    } else if (H->opts.smoother == CPM_SMOOTH_RBGS) {
+      level_op<T>(H, W, l, LAP_JAC_RED, f, u, nullptr, nullptr, st);
+      level_op<T>(H, W, l, LAP_JAC_BLACK, f, u, nullptr, nullptr, st);
     } else {
-      launch_extend<T>(v, u, w.w.get(), (int32_t)v.nplus, st);
-      launch_lap<T>(v, LAP_JACOBI, u, w.w.get(), f, lv.cvec<T>(), cval, lv.dA<T>(), omega, nullptr,
-                    u, nullptr, 0, st);
+      level_op<T>(H, W, l, LAP_JACOBI, f, u, nullptr, nullptr, st);
     }
   }
 }
@@ -273,15 +342,11 @@ static void transfer_residual(cpm_hier_s* H, Workspace& W, int l, const T* f, co
   if (H->opts.smoother == CPM_SMOOTH_RM) {
     launch_rm_resid<T>(v, u, f, lv.cvec<T>(), (T)H->c, r, st);
   } else if (H->opts.residual_mode == 1) {
-    launch_extend<T>(v, u, w.w.get(), (int32_t)v.nplus, st);
-    launch_lap<T>(v, LAP_RESID, u, w.w.get(), f, lv.cvec<T>(), (T)H->c, nullptr, T(0), r, nullptr,
-                  nullptr, 0, st);
+    level_op<T>(H, W, l, LAP_RESID, f, u, r, nullptr, st);
   } else {
     // f - A (E u): first E u on B, then the residual of that re-extended iterate
     launch_extend<T>(v, u, w.tmp.get(), v.nB, st);
-    launch_extend<T>(v, w.tmp.get(), w.w.get(), (int32_t)v.nplus, st);
-    launch_lap<T>(v, LAP_RESID, w.tmp.get(), w.w.get(), f, lv.cvec<T>(), (T)H->c, nullptr, T(0), r,
-                  nullptr, nullptr, 0, st);
+    level_op<T>(H, W, l, LAP_RESID, f, w.tmp.get(), r, nullptr, st);
   }
 }
 
@@ -309,12 +374,8 @@ static void coarse_solve(cpm_hier_s* H, Workspace* const* W, int G, const T* con
       const double* r[kMaxGroup];
       for (int g = 0; g < G; ++g) r[g] = W[g]->w64[l].r.get();
       for (int it = 0; it < 2; ++it) {
-        for (int g = 0; g < G; ++g) {
-          Work<double>& w = W[g]->w64[l];
-          launch_extend<double>(v, u[g], w.w.get(), (int32_t)v.nplus, st);
-          launch_lap<double>(v, LAP_RESID, u[g], w.w.get(), f[g], lv.c64.get(), H->c, nullptr, 0.0,
-                             w.r.get(), nullptr, nullptr, 0, st);
-        }
+        for (int g = 0; g < G; ++g)
+          level_op<double>(H, *W[g], l, LAP_RESID, f[g], u[g], W[g]->w64[l].r.get(), nullptr, st);
         launch_coarse_gemv32<double>(H->Ainv32.get(), r, u, G, H->nc, true, st);
       }
     }
@@ -324,12 +385,8 @@ static void coarse_solve(cpm_hier_s* H, Workspace* const* W, int G, const T* con
   const LevelView<T> v = lv.view<T>();
   for (int g = 0; g < G; ++g) {
     CPM_CUDA_TRY(cudaMemsetAsync(u[g], 0, sizeof(T) * lv.lev->nB, st));
-    Work<T>& w = W[g]->work<T>(l);
-    for (int s = 0; s < H->coarse_sweeps; ++s) {
-      launch_extend<T>(v, u[g], w.w.get(), (int32_t)v.nplus, st);
-      launch_lap<T>(v, LAP_JACOBI, u[g], w.w.get(), f[g], lv.cvec<T>(), (T)H->c, lv.dA<T>(),
-                    (T)H->opts.omega, nullptr, u[g], nullptr, 0, st);
-    }
+    for (int s = 0; s < H->coarse_sweeps; ++s)
+      level_op<T>(H, *W[g], l, LAP_JACOBI, f[g], u[g], nullptr, nullptr, st);
   }
 }
 
@@ -370,7 +427,10 @@ static void vcycle_level(cpm_hier_s* H, Workspace* const* W, int G, int l, const
     cf[g] = cw.f.get();
     cu[g] = cw.u.get();
   }
-  vcycle_level<T>(H, W, G, l + 1, cf, cu, st);
+  // V-cycle: one cycle of the next level from zero; W-cycle: a second one
+  // from the first's result (the coarsest level is solved once)
+  const int ncyc = l + 1 == nl - 1 ? 1 : H->opts.cycle;
+  for (int q = 0; q < ncyc; ++q) vcycle_level<T>(H, W, G, l + 1, cf, cu, st);
   for (int g = 0; g < G; ++g) {
     launch_transfer<T>(tview<T>(lv.P, lv.lev->dim), cu[g], u[g], true, st);
     smooth<T>(H, *W[g], l, f[g], u[g], H->opts.nu2, st);
@@ -383,6 +443,30 @@ static void vcycle_level(cpm_hier_s* H, Workspace& W, int l, const T* f, T* u, c
   vcycle_level<T>(H, &w, 1, l, &f, &u, st);
 }
 
+// Full multigrid from zero (remark at Algorithm 4.1): f restricted to every
+// level (into the levels' work f), the coarsest level solved, then on each
+// finer level the prolonged coarse solution starts one cycle of that level.
+// A level's work f and u are free again once the level above has taken its
+// start value from them.
+template <typename T>
+static void fmg(cpm_hier_s* H, Workspace& W, const T* f, T* u, cudaStream_t st) {
+  const int nl = (int)H->L.size();
+  std::vector<const T*> fl(nl);
+  fl[0] = f;
+  for (int l = 0; l + 1 < nl; ++l) {
+    launch_transfer<T>(tview<T>(H->L[l].R, H->L[l].lev->dim), fl[l], W.work<T>(l + 1).f.get(), false, st);
+    fl[l + 1] = W.work<T>(l + 1).f.get();
+  }
+  T* uc = nl == 1 ? u : W.work<T>(nl - 1).u.get();
+  Workspace* w = &W;
+  coarse_solve<T>(H, &w, 1, &fl[nl - 1], &uc, st);
+  for (int l = nl - 2; l >= 0; --l) {
+    T* ul = l == 0 ? u : W.work<T>(l).u.get();
+    launch_transfer<T>(tview<T>(H->L[l].P, H->L[l].lev->dim), W.work<T>(l + 1).u.get(), ul, false, st);
+    vcycle_level<T>(H, W, l, fl[l], ul, st);
+  }
+}
+
 // FP64 outer residual r = f - A u on the finest level with norms into W.norms,
 // in the relative form (differences formed from exact inputs; its rounding
 // floor is far below that of w = E u followed by the stencil at fine dx).
@@ -390,15 +474,20 @@ static void outer_residual(cpm_hier_s* H, Workspace& W, const double* f, const d
                            cudaStream_t st) {
   HLevel& lv = H->L[0];
   const LevelView<double> v = lv.view<double>();
+  if (H->opts.op_form != CPM_OP_MBR) {  // direct form of Eq. 3.3
+    level_op<double>(H, W, 0, LAP_RESID, f, u, r, W.part.get(), st);
+    launch_norm_final(W.part.get(), paper_blocks(v), W.norms, st);
+    return;
+  }
   launch_extend_rel(v, u, W.w64[0].w.get(), W.refv.get(), st);
   launch_resid_rel(v, u, W.w64[0].w.get(), W.refv.get(), f, lv.c64.get(), H->c, r, W.part.get(), st);
-  launch_norm_final(W.part.get(), nblk(v.nB, 256), W.norms, st);
+  launch_norm_final(W.part.get(), lap_blocks_f64(v), W.norms, st);
 }
 
 // One outer iteration after the residual, for G systems of one hierarchy in
 // lockstep: u += V(0, r), then the new residual.
 static void outer_step(cpm_hier_s* H, Workspace* const* W, int G, int mode, int inner,
-                       cudaStream_t st) {
+                       cudaStream_t st, bool first_fmg = false) {
   const int64_t nB = H->L[0].lev->nB;
   if (mode == CPM_SOLVE_F64) {
     const double* r[kMaxGroup];
@@ -408,7 +497,10 @@ static void outer_step(cpm_hier_s* H, Workspace* const* W, int G, int mode, int 
       r[g] = W[g]->r64.get();
       d[g] = W[g]->d64.get();
     }
-    vcycle_level<double>(H, W, G, 0, r, d, st);
+    if (first_fmg)
+      for (int g = 0; g < G; ++g) fmg<double>(H, *W[g], r[g], d[g], st);
+    else
+      vcycle_level<double>(H, W, G, 0, r, d, st);
     for (int g = 0; g < G; ++g) launch_axpy64(W[g]->u_own.get(), W[g]->d64.get(), nB, st);
   } else {
     const float* r[kMaxGroup];
@@ -419,16 +511,22 @@ static void outer_step(cpm_hier_s* H, Workspace* const* W, int G, int mode, int 
       r[g] = W[g]->r32.get();
       d[g] = W[g]->d32.get();
     }
-    for (int j = 0; j < inner; ++j) vcycle_level<float>(H, W, G, 0, r, d, st);
+    for (int j = 0; j < inner; ++j) {
+      if (first_fmg && j == 0)
+        for (int g = 0; g < G; ++g) fmg<float>(H, *W[g], r[g], d[g], st);
+      else
+        vcycle_level<float>(H, W, G, 0, r, d, st);
+    }
     for (int g = 0; g < G; ++g) launch_axpy_scaled(W[g]->u_own.get(), W[g]->d32.get(), W[g]->norms, nB, st);
   }
   for (int g = 0; g < G; ++g)
     outer_residual(H, *W[g], W[g]->f_own.get(), W[g]->u_own.get(), W[g]->r64.get(), st);
 }
 
-static void outer_step(cpm_hier_s* H, Workspace& W, int mode, int inner, cudaStream_t st) {
+static void outer_step(cpm_hier_s* H, Workspace& W, int mode, int inner, cudaStream_t st,
+                       bool first_fmg = false) {
   Workspace* w = &W;
-  outer_step(H, &w, 1, mode, inner, st);
+  outer_step(H, &w, 1, mode, inner, st, first_fmg);
 }
 
 }  // namespace cpm
@@ -473,8 +571,8 @@ const char* cpm_last_error(void) { return cpm::g_last_error.c_str(); }
 
 static void check_surface(const cpm_surface* s) {
   CPM_CHECK(s != nullptr, CPM_ERR_ARG, "surface is NULL");
-  CPM_CHECK(s->kind >= CPM_CIRCLE && s->kind <= CPM_ELLIPSOID, CPM_ERR_ARG, "unknown surface kind");
-  const int np = s->kind == CPM_TORUS ? 2 : (s->kind == CPM_ELLIPSOID ? 3 : 1);
+  CPM_CHECK(s->kind >= CPM_CIRCLE && s->kind <= CPM_DZIUK, CPM_ERR_ARG, "unknown surface kind");
+  const int np = s->kind == CPM_TORUS ? 2 : (s->kind == CPM_ELLIPSOID ? 3 : (s->kind == CPM_DZIUK ? 0 : 1));
   for (int i = 0; i < np; ++i)
     CPM_CHECK(s->param[i] > 0 && std::isfinite(s->param[i]), CPM_ERR_ARG,
               "surface parameters must be positive");
@@ -544,6 +642,13 @@ cpm_status cpm_band_export(cpm_band band, int32_t* ijk, double* cp, int32_t* ste
   CPM_API_END
 }
 
+cpm_status cpm_band_counts(cpm_band band, int64_t* counts, cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(band != nullptr && counts != nullptr, CPM_ERR_ARG, "NULL argument");
+  band_counts(band->lev, (cudaStream_t)stream, counts);
+  CPM_API_END
+}
+
 cpm_status cpm_band_destroy(cpm_band band) {
   CPM_API_BEGIN
   delete band;
@@ -561,23 +666,33 @@ static void copy_level(const Level& a, Level& b, cudaStream_t st) {
                                    cudaMemcpyDeviceToDevice, st));
   };
   cp(b.map, a.map); cp(b.bmask, a.bmask); cp(b.gmask, a.gmask); cp(b.bstart, a.bstart);
-  cp(b.gstart, a.gstart); cp(b.bcoord, a.bcoord); cp(b.key, a.key); cp(b.cp, a.cp);
+  cp(b.gstart, a.gstart); cp(b.bcoord, a.bcoord); cp(b.brec, a.brec); cp(b.key, a.key); cp(b.cp, a.cp);
   cp(b.fr64, a.fr64); cp(b.fr32, a.fr32);
   b.ntiles = a.ntiles;
   cp(b.tile_brick, a.tile_brick); cp(b.tile_box, a.tile_box); cp(b.tile_mask, a.tile_mask); cp(b.tile_bstart, a.tile_bstart); cp(b.tile_start, a.tile_start); cp(b.tile_mid, a.tile_mid); cp(b.erec, a.erec);
   cp(b.efr32, a.efr32); cp(b.ew64, a.ew64); cp(b.nbr, a.nbr);
+  b.nchunks = a.nchunks;
+  cp(b.echunk, a.echunk); cp(b.tile_cstart, a.tile_cstart); cp(b.tile_cmid, a.tile_cmid);
 }
 
-static void build_transfer(const Level& target, const Level& src, Transfer& t, cudaStream_t st,
-                           int32_t* err) {
+static void build_transfer(const Level& target, const Level& src, Transfer& t, int deg,
+                           cudaStream_t st, int32_t* err) {
   t.n = target.nB;
-  t.src_idx.alloc((size_t)(target.dim == 3 ? 8 : 4) * t.n);
+  t.src = src.view();
+  t.deg = deg;
+  t.base.alloc((size_t)t.n);
   t.fr64.alloc((size_t)target.dim * t.n);
   t.fr32.alloc((size_t)target.dim * t.n);
-  k_transfer_records<<<nblk(t.n, 256), 256, 0, st>>>(target.cp.get(), target.nplus(), t.n, target.dim,
-                                                     src.lo, src.dx, src.view(), t.src_idx.get(),
+  k_transfer_records<<<nblk(t.n, 256), 256, 0, st>>>(target.cp.get(), target.nplus(), t.n, target.dim, deg,
+                                                     src.lo, src.dx, src.view(), t.base.get(),
                                                      t.fr64.get(), t.fr32.get(), err);
   CPM_CUDA_TRY(cudaGetLastError());
+  if (CPM_TRANSFER_INDEXED && deg == 1 && t.n > 0) {
+    t.idx.alloc((size_t)(target.dim == 3 ? 8 : 4) * t.n);
+    k_transfer_index<<<nblk(t.n, 256), 256, 0, st>>>(t.base.get(), t.n, target.dim, src.view(),
+                                                     t.idx.get());
+    CPM_CUDA_TRY(cudaGetLastError());
+  }
 }
 
 cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_stream stream,
@@ -591,10 +706,20 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
   if (o.nu1 <= 0 && o.nu2 <= 0) { o.nu1 = 3; o.nu2 = 3; }
   if (o.omega <= 0) o.omega = 0.8;
   if (o.transfer_deg == 0) o.transfer_deg = 1;
-  CPM_CHECK(o.transfer_deg == 1, CPM_ERR_ARG, "only linear transfers (degree 1) are implemented");
-  CPM_CHECK(o.smoother == CPM_SMOOTH_JACOBI || o.smoother == CPM_SMOOTH_RM, CPM_ERR_ARG,
-            "unknown smoother");
+  CPM_CHECK(o.transfer_deg == 1 || o.transfer_deg == 3, CPM_ERR_ARG,
+            "transfer_deg must be 1 (linear) or 3 (cubic)");
+  CPM_CHECK(o.smoother == CPM_SMOOTH_JACOBI || o.smoother == CPM_SMOOTH_RM ||
+                o.smoother == CPM_SMOOTH_RBGS,
+            CPM_ERR_ARG, "unknown smoother");
+  if (o.cycle == 0) o.cycle = 1;
+  CPM_CHECK(o.cycle == 1 || o.cycle == 2, CPM_ERR_ARG, "cycle must be 1 (V) or 2 (W)");
   CPM_CHECK(o.nu1 >= 0 && o.nu2 >= 0 && o.nu1 + o.nu2 <= 64, CPM_ERR_ARG, "bad sweep counts");
+  CPM_CHECK(o.op_form == CPM_OP_MBR || o.op_form == CPM_OP_PAPER || o.op_form == CPM_OP_VARDIFF,
+            CPM_ERR_ARG, "unknown op_form");
+  CPM_CHECK((o.op_form == CPM_OP_VARDIFF) == (o.a_device != nullptr), CPM_ERR_ARG,
+            "a_device is given exactly with op_form CPM_OP_VARDIFF");
+  CPM_CHECK(o.op_form == CPM_OP_MBR || o.smoother != CPM_SMOOTH_RM, CPM_ERR_ARG,
+            "the paper-form operator is smoothed on A (Jacobi or red-black Gauss-Seidel)");
   if (!(o.c > 0)) o.c = 1.0;
   CPM_CHECK(std::isfinite(o.c), CPM_ERR_ARG, "c must be finite");
   std::unique_ptr<cpm_hier_s> H(new cpm_hier_s);
@@ -672,8 +797,8 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
   DBuf<int32_t> err(1);
   CPM_CUDA_TRY(cudaMemsetAsync(err.get(), 0, sizeof(int32_t), st));
   for (int l = 0; l + 1 < nl; ++l) {
-    build_transfer(*H->L[l + 1].lev, *H->L[l].lev, H->L[l].R, st, err.get());
-    build_transfer(*H->L[l].lev, *H->L[l + 1].lev, H->L[l].P, st, err.get());
+    build_transfer(*H->L[l + 1].lev, *H->L[l].lev, H->L[l].R, o.transfer_deg, st, err.get());
+    build_transfer(*H->L[l].lev, *H->L[l + 1].lev, H->L[l].P, o.transfer_deg, st, err.get());
   }
   // per-point c on every level (restricted from the finest band)
   if (o.c_device) {
@@ -691,11 +816,30 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
       launch_cast_from_f64<float>(lv.c64.get(), lv.c32.get(), lv.lev->nB, st);
     }
   }
+  // diffusion coefficient on every level (restricted from the finest band)
+  if (o.a_device) {
+    H->L[0].a64.alloc(f0.nB);
+    CPM_CUDA_TRY(cudaMemcpyAsync(H->L[0].a64.get(), o.a_device, sizeof(double) * f0.nB,
+                                 cudaMemcpyDeviceToDevice, st));
+    for (int l = 0; l + 1 < nl; ++l) {
+      HLevel& a = H->L[l];
+      HLevel& b = H->L[l + 1];
+      b.a64.alloc(b.lev->nB);
+      launch_transfer<double>(tview<double>(a.R, a.lev->dim), a.a64.get(), b.a64.get(), false, st);
+    }
+    for (auto& lv : H->L) {
+      lv.a32.alloc(lv.lev->nB);
+      launch_cast_from_f64<float>(lv.a64.get(), lv.a32.get(), lv.lev->nB, st);
+    }
+  }
   // diag(A) = c - diag(M), work buffers
   for (auto& lv : H->L) {
     const int64_t nB = lv.lev->nB, np = lv.lev->nplus();
     DBuf<double> dM(nB);
-    launch_diag_M(lv.view<double>(), dM.get(), st);
+    if (o.op_form != CPM_OP_MBR)
+      launch_diag_Mp(lv.view<double>(), dM.get(), lv.a64.get(), st);
+    else
+      launch_diag_M(lv.view<double>(), dM.get(), st);
     lv.dA64.alloc(nB);
     lv.dA32.alloc(nB);
     k_diag_A<<<nblk(nB, 256), 256, 0, st>>>(dM.get(), lv.c64.get(), H->c, o.omega, lv.dA64.get(),
@@ -710,15 +854,23 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
   if (H->coarse_mode == 0) {
     H->Ainv.alloc(nn);
     CPM_CUDA_TRY(cudaMemsetAsync(H->Ainv.get(), 0, sizeof(double) * nn, st));
-    launch_assemble_A<double>(H->L[nl - 1].view<double>(), H->L[nl - 1].c64.get(), H->c,
-                              H->Ainv.get(), st);
+    if (o.op_form != CPM_OP_MBR)
+      launch_assemble_Ap<double>(H->L[nl - 1].view<double>(), H->L[nl - 1].c64.get(), H->c,
+                                 H->Ainv.get(), H->L[nl - 1].a64.get(), st);
+    else
+      launch_assemble_A<double>(H->L[nl - 1].view<double>(), H->L[nl - 1].c64.get(), H->c,
+                                H->Ainv.get(), st);
     CPM_CUDA_TRY(cudaGetLastError());
     invert_dense(H->Ainv.get(), H->nc, st, err.get());
   } else if (H->coarse_mode == 1) {
     DBuf<float> A32(nn);
     CPM_CUDA_TRY(cudaMemsetAsync(A32.get(), 0, sizeof(float) * nn, st));
-    launch_assemble_A<float>(H->L[nl - 1].view<double>(), H->L[nl - 1].c64.get(), H->c, A32.get(),
-                             st);
+    if (o.op_form != CPM_OP_MBR)
+      launch_assemble_Ap<float>(H->L[nl - 1].view<double>(), H->L[nl - 1].c64.get(), H->c,
+                                A32.get(), H->L[nl - 1].a64.get(), st);
+    else
+      launch_assemble_A<float>(H->L[nl - 1].view<double>(), H->L[nl - 1].c64.get(), H->c,
+                               A32.get(), st);
     CPM_CUDA_TRY(cudaGetLastError());
     H->Ainv32.alloc(nn);
     invert_dense_f32(A32.get(), H->Ainv32.get(), H->nc, st, err.get());
@@ -752,18 +904,11 @@ cpm_status cpm_apply(cpm_hier h, int32_t level, int32_t prec, const void* u, voi
   CPM_CHECK(h != nullptr && u != nullptr && Mu != nullptr, CPM_ERR_ARG, "NULL argument");
   CPM_CHECK(level >= 0 && level < (int)h->L.size(), CPM_ERR_ARG, "level out of range");
   cudaStream_t st = (cudaStream_t)stream;
-  HLevel& lv = h->L[level];
   if (prec == CPM_F64) {
-    const auto v = lv.view<double>();
-    launch_extend<double>(v, (const double*)u, h->ws.w64[level].w.get(), (int32_t)v.nplus, st);
-    launch_lap<double>(v, LAP_APPLY, (const double*)u, h->ws.w64[level].w.get(), nullptr, nullptr, 0.0, nullptr,
-                       0.0, (double*)Mu, nullptr, nullptr, 0, st);
+    level_op<double>(h, h->ws, level, LAP_APPLY, nullptr, (const double*)u, (double*)Mu, nullptr, st);
   } else {
     CPM_CHECK(prec == CPM_F32, CPM_ERR_ARG, "unknown precision");
-    const auto v = lv.view<float>();
-    launch_extend<float>(v, (const float*)u, h->ws.w32[level].w.get(), (int32_t)v.nplus, st);
-    launch_lap<float>(v, LAP_APPLY, (const float*)u, h->ws.w32[level].w.get(), nullptr, nullptr, 0.f, nullptr,
-                      0.f, (float*)Mu, nullptr, nullptr, 0, st);
+    level_op<float>(h, h->ws, level, LAP_APPLY, nullptr, (const float*)u, (float*)Mu, nullptr, st);
   }
   CPM_CUDA_TRY(cudaGetLastError());
   CPM_API_END
@@ -852,6 +997,8 @@ cpm_status cpm_residual_norms_noalloc(cpm_hier h, const double* f, const double*
   CPM_API_BEGIN
   CPM_CHECK(h != nullptr && u != nullptr && f != nullptr && norms != nullptr, CPM_ERR_ARG,
             "NULL argument");
+  CPM_CHECK(h->opts.op_form == CPM_OP_MBR, CPM_ERR_ARG,
+            "cpm_residual_norms_noalloc evaluates the CPM_OP_MBR operator only");
   const HLevel& lv = h->L[0];
   residual_norms_noalloc(lv.view<double>(), f, u, lv.c64.get(), h->c, norms, (cudaStream_t)stream);
   CPM_API_END
@@ -926,7 +1073,13 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
   launch_norm_partials<double>(W.f_own.get(), nB, W.part.get(), st);
   launch_norm_final(W.part.get(), kNormBlocks, W.normf.get(), st);
   CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned + 4, W.normf.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
-  outer_residual(h, W, W.f_own.get(), W.u_own.get(), W.r64.get(), st);
+  if (o.zero_init) {  // u = 0: the residual is f itself, and so are its norms
+    CPM_CUDA_TRY(cudaMemcpyAsync(W.r64.get(), W.f_own.get(), nB * sizeof(double),
+                                 cudaMemcpyDeviceToDevice, st));
+    CPM_CUDA_TRY(cudaMemcpyAsync(W.norms, W.normf.get(), 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  } else {
+    outer_residual(h, W, W.f_own.get(), W.u_own.get(), W.r64.get(), st);
+  }
   CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.norms, sizeof(double), cudaMemcpyDeviceToHost, st));
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
   const double fmax = W.pinned[4];
@@ -955,7 +1108,9 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
     if (o.learned && it == 1 && !rep.fallback) learned_on = true;
     h->learned_active = learned_on;
     gi = learned_on ? 2 : o.mode;
-    if (o.use_graph) {
+    if (o.fmg && it == 0) {
+      outer_step(h, W, o.mode, o.inner_cycles, st, true);
+    } else if (o.use_graph) {
       capture_outer_step(h, W, gi, o.mode, o.inner_cycles, st);
       CPM_CUDA_TRY(cudaGraphLaunch(W.graph[gi], st));
       count_launch(W.graph_kernels[gi]);
@@ -1074,6 +1229,8 @@ cpm_status cpm_hier_set_smoother(cpm_hier h, cpm_mlp m) {
   h->mlp = m;
   if (m && !h->mlpd) {
     CPM_CHECK(h->L[0].lev->dim == 3, CPM_ERR_ARG, "the learned smoother is for surfaces in 3-D");
+    CPM_CHECK(h->opts.op_form == CPM_OP_MBR, CPM_ERR_ARG,
+              "the learned smoother is trained on the CPM_OP_MBR operator");
     h->mlpd.reset(new MlpLevelData);
     h->mlpd->build(*h->L[0].lev, h->L[0].dM64.get(), h->ws.hs);
     CPM_CUDA_TRY(cudaStreamSynchronize(h->ws.hs));
@@ -1129,6 +1286,147 @@ cpm_status cpm_mlp_train_step(cpm_hier h, const float* r, float lr, double* loss
     CPM_CUDA_TRY(cudaStreamSynchronize(st));
     *loss = l2[1] > 0 ? l2[0] / l2[1] : 0.0;
   }
+  CPM_API_END
+}
+
+cpm_status cpm_mlp_train(cpm_mlp m, const cpm_train_set* set, const cpm_train_opts* opts_in,
+                         cpm_train_report* report, cpm_stream stream) {
+  CPM_API_BEGIN
+  CPM_CHECK(m != nullptr && set != nullptr && set->n_fields > 0 && set->hier != nullptr &&
+                set->r != nullptr,
+            CPM_ERR_ARG, "cpm_mlp_train: NULL or empty training set");
+  cpm_train_opts o{};
+  if (opts_in) o = *opts_in;
+  if (o.steps <= 0) o.steps = 400;
+  if (!(o.lr > 0)) o.lr = 2e-3f;
+  if (!(o.lr_final > 0)) o.lr_final = o.lr;
+  CPM_CHECK(std::isfinite(o.lr) && std::isfinite(o.lr_final), CPM_ERR_ARG, "learning rate not finite");
+  const auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t st = (cudaStream_t)stream;
+  const int nf = set->n_fields;
+  int32_t maxB = 0;
+  int64_t maxP = 0;
+  for (int k = 0; k < nf; ++k) {
+    cpm_hier h = set->hier[k];
+    CPM_CHECK(h != nullptr && set->r[k] != nullptr, CPM_ERR_ARG, "cpm_mlp_train: NULL field");
+    CPM_CHECK(h->L[0].lev->dim == 3, CPM_ERR_ARG, "the learned smoother is for surfaces in 3-D");
+    if (h->mlp != m || !h->mlpd) {
+      const cpm_status sm = cpm_hier_set_smoother(h, m);
+      if (sm != CPM_OK) return sm;
+    }
+    maxB = std::max(maxB, h->L[0].lev->nB);
+    maxP = std::max(maxP, h->L[0].lev->nplus());
+  }
+  if (o.reset) {
+    CPM_CUDA_TRY(cudaMemsetAsync(m->m.get(), 0, kNParams * sizeof(float), st));
+    CPM_CUDA_TRY(cudaMemsetAsync(m->v.get(), 0, kNParams * sizeof(float), st));
+    m->step = 0;
+  }
+  m->tb.ensure(maxB, maxP);
+  // the fields scaled by 1 / max|r| into FP32
+  std::vector<DBuf<float>> f32(nf);
+  DBuf<double> norms(4 * (size_t)nf), part(2 * (size_t)kNormBlocks);
+  for (int k = 0; k < nf; ++k) {
+    const int32_t nB = set->hier[k]->L[0].lev->nB;
+    f32[k].alloc(nB);
+    launch_norm_partials<double>(set->r[k], nB, part.get(), st);
+    launch_norm_final(part.get(), kNormBlocks, norms.get() + 4 * (size_t)k, st);
+    launch_scale_to_f32(set->r[k], norms.get() + 4 * (size_t)k, f32[k].get(), nB, st);
+  }
+  std::vector<double> hn(4 * (size_t)nf);
+  CPM_CUDA_TRY(cudaMemcpyAsync(hn.data(), norms.get(), hn.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int k = 0; k < nf; ++k)
+    CPM_CHECK(std::isfinite(hn[4 * (size_t)k]) && hn[4 * (size_t)k] > 0, CPM_ERR_ARG,
+              "cpm_mlp_train: a field is zero or not finite");
+  auto mean_loss = [&]() {
+    double acc = 0.0;
+    for (int k = 0; k < nf; ++k) {
+      mlp_loss_grad_host(set->hier[k], f32[k].get(), st);
+      double l2[2];
+      CPM_CUDA_TRY(cudaMemcpyAsync(l2, m->tb.loss.get(), sizeof(l2), cudaMemcpyDeviceToHost, st));
+      CPM_CUDA_TRY(cudaStreamSynchronize(st));
+      acc += l2[1] > 0 ? l2[0] / l2[1] : 0.0;
+    }
+    return acc / nf;
+  };
+  const double loss_first = mean_loss();
+  const int per = std::max(1, o.steps / nf);
+  int step = 0, k = 0;
+  while (step < o.steps) {
+    for (int j = 0; j < per && step < o.steps; ++j, ++step) {
+      const float frac = o.steps > 1 ? (float)step / (float)(o.steps - 1) : 0.f;
+      const float lr = o.lr + (o.lr_final - o.lr) * frac;
+      mlp_loss_grad_host(set->hier[k], f32[k].get(), st);
+      ++m->step;
+      mlp_adam(m->params.get(), m->tb.grad.get(), m->m.get(), m->v.get(), m->step, lr, st);
+    }
+    k = (k + 1) % nf;
+  }
+  CPM_CUDA_TRY(cudaGetLastError());
+  const double loss_last = mean_loss();
+  if (report) {
+    report->steps = o.steps;
+    report->n_fields = nf;
+    report->loss_first = loss_first;
+    report->loss_last = loss_last;
+    report->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  }
+  CPM_API_END
+}
+
+static const char kMlpMagic[8] = {'C', 'P', 'M', 'M', 'L', 'P', '0', '1'};
+
+cpm_status cpm_mlp_save(cpm_mlp m, const char* path) {
+  CPM_API_BEGIN
+  CPM_CHECK(m != nullptr && path != nullptr, CPM_ERR_ARG, "NULL argument");
+  std::vector<float> buf(3 * (size_t)kNParams);
+  CPM_CUDA_TRY(cudaDeviceSynchronize());
+  CPM_CUDA_TRY(cudaMemcpy(buf.data(), m->params.get(), kNParams * sizeof(float), cudaMemcpyDeviceToHost));
+  CPM_CUDA_TRY(cudaMemcpy(buf.data() + kNParams, m->m.get(), kNParams * sizeof(float),
+                          cudaMemcpyDeviceToHost));
+  CPM_CUDA_TRY(cudaMemcpy(buf.data() + 2 * kNParams, m->v.get(), kNParams * sizeof(float),
+                          cudaMemcpyDeviceToHost));
+  FILE* fp = std::fopen(path, "wb");
+  CPM_CHECK(fp != nullptr, CPM_ERR_ARG, std::string("cannot open ") + path + " for writing");
+  const int32_t n = kNParams;
+  const int64_t step = m->step;
+  bool ok = std::fwrite(kMlpMagic, 1, 8, fp) == 8 && std::fwrite(&n, sizeof(n), 1, fp) == 1 &&
+            std::fwrite(&step, sizeof(step), 1, fp) == 1 &&
+            std::fwrite(buf.data(), sizeof(float), buf.size(), fp) == buf.size();
+  ok = (std::fclose(fp) == 0) && ok;
+  CPM_CHECK(ok, CPM_ERR_ARG, std::string("short write to ") + path);
+  CPM_API_END
+}
+
+cpm_status cpm_mlp_load(const char* path, cpm_mlp* out) {
+  CPM_API_BEGIN
+  CPM_CHECK(path != nullptr && out != nullptr, CPM_ERR_ARG, "NULL argument");
+  *out = nullptr;
+  FILE* fp = std::fopen(path, "rb");
+  CPM_CHECK(fp != nullptr, CPM_ERR_ARG, std::string("cannot open ") + path);
+  char magic[8];
+  int32_t n = 0;
+  int64_t step = 0;
+  std::vector<float> buf(3 * (size_t)kNParams);
+  bool ok = std::fread(magic, 1, 8, fp) == 8 && std::memcmp(magic, kMlpMagic, 8) == 0 &&
+            std::fread(&n, sizeof(n), 1, fp) == 1 && n == kNParams &&
+            std::fread(&step, sizeof(step), 1, fp) == 1 && step >= 0 &&
+            std::fread(buf.data(), sizeof(float), buf.size(), fp) == buf.size();
+  std::fclose(fp);
+  CPM_CHECK(ok, CPM_ERR_ARG, std::string(path) + " is not a network written by cpm_mlp_save");
+  cpm_mlp m = nullptr;
+  const cpm_status cs = cpm_mlp_create(0, &m);
+  if (cs != CPM_OK) return cs;
+  std::unique_ptr<cpm_mlp_s> guard(m);
+  CPM_CUDA_TRY(cudaMemcpy(m->params.get(), buf.data(), kNParams * sizeof(float), cudaMemcpyHostToDevice));
+  CPM_CUDA_TRY(cudaMemcpy(m->m.get(), buf.data() + kNParams, kNParams * sizeof(float),
+                          cudaMemcpyHostToDevice));
+  CPM_CUDA_TRY(cudaMemcpy(m->v.get(), buf.data() + 2 * kNParams, kNParams * sizeof(float),
+                          cudaMemcpyHostToDevice));
+  m->step = step;
+  *out = guard.release();
   CPM_API_END
 }
 
@@ -1337,6 +1635,7 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
   CPM_CHECK(b != nullptr && f != nullptr && u != nullptr, CPM_ERR_ARG, "NULL argument");
   const cpm_solve_opts o = solve_opts(opts_in);
   CPM_CHECK(!o.learned, CPM_ERR_ARG, "learned smoothing is not available in batches");
+  CPM_CHECK(!o.fmg, CPM_ERR_ARG, "full multigrid is not available in batches");
   const int ns = (int)b->H.size();
   for (int s = 0; s < ns; ++s)
     CPM_CHECK(f[s] != nullptr && u[s] != nullptr, CPM_ERR_ARG, "NULL vector in batch");
@@ -1358,7 +1657,14 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
       CPM_CUDA_TRY(cudaMemcpyAsync(W.u_own.get(), u[s], nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
     launch_norm_partials<double>(W.f_own.get(), nB, W.part.get(), st);
     launch_norm_final(W.part.get(), kNormBlocks, fn_all.get() + 4 * (size_t)s, st);
-    outer_residual(b->H[s], W, W.f_own.get(), W.u_own.get(), W.r64.get(), st);
+    if (o.zero_init) {  // u = 0: the residual is f itself, and so are its norms
+      CPM_CUDA_TRY(cudaMemcpyAsync(W.r64.get(), W.f_own.get(), nB * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+      CPM_CUDA_TRY(cudaMemcpyAsync(W.norms, fn_all.get() + 4 * (size_t)s, 3 * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+    } else {
+      outer_residual(b->H[s], W, W.f_own.get(), W.u_own.get(), W.r64.get(), st);
+    }
   }
   for (int k = 0; k < kMaxBranches; ++k) {
     CPM_CUDA_TRY(cudaEventRecord(b->ev_join[k], b->fs[k]));

@@ -238,76 +238,81 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_mlp_forward(MlpFwdArgs A) {
 }
 
 // ----------------------------------------------------------------- backward
-// Per CTA of kBwdPts points: dz2 = dy w3 [h2 > 0], dz1 = (dz2 W2^T) [h1 > 0],
-// partial gradients written to part[blockIdx.x][kNParams] (fixed order).
+// A fixed grid of CTAs; each loops over groups of kBwdPts points: dz2 = dy w3
+// [h2 > 0], dz1 = (dz2 W2^T) [h1 > 0], and every thread accumulates the
+// gradient entries it owns (parameter q = threadIdx.x + k * kBwdThreads) over
+// all of the CTA's groups in registers.  Each CTA writes one partial gradient
+// (part[blockIdx.x][kNParams]), summed in a fixed order by k_grad_reduce, so
+// the partials take kBwdCtas x 25 KB whatever the band size.
 constexpr int kBwdPts = 32;
 constexpr int kBwdThreads = 256;
+constexpr int kBwdCtas = 2 * 152;
+constexpr int kBwdPer = (kNParams + kBwdThreads - 1) / kBwdThreads;  // 25 entries per thread
 
 __global__ void __launch_bounds__(kBwdThreads) k_mlp_backward(const float* params, const float* dy,
                                                               const __nv_bfloat16* Xs,
                                                               const __nv_bfloat16* H1,
                                                               const __nv_bfloat16* H2, int32_t nB,
                                                               float* part) {
-  __shared__ float x[kBwdPts][33], h1[kBwdPts][65], dz2[kBwdPts][65], dz1[kBwdPts][65];
+  __shared__ float x[kBwdPts][33], h1[kBwdPts][65], h2[kBwdPts][65], dz2[kBwdPts][65],
+      dz1[kBwdPts][65];
   __shared__ float dys[kBwdPts];
-  const int64_t p0 = (int64_t)blockIdx.x * kBwdPts;
-  for (int q = threadIdx.x; q < kBwdPts * 64; q += blockDim.x) {
-    const int p = q >> 6, j = q & 63;
-    const int64_t gp = p0 + p;
-    const bool ok = gp < nB;
-    const float dyv = ok ? dy[gp] : 0.f;
-    const float h2v = ok ? __bfloat162float(H2[gp * 64 + j]) : 0.f;
-    h1[p][j] = ok ? __bfloat162float(H1[gp * 64 + j]) : 0.f;
-    dz2[p][j] = h2v > 0.f ? dyv * params[kOffW3 + j] : 0.f;
-    if (j < 32) x[p][j] = ok ? __bfloat162float(Xs[gp * 32 + j]) : 0.f;
-    if (j == 0) dys[p] = dyv;
-  }
-  __syncthreads();
-  // dz1 = (dz2 W2^T) * [h1 > 0]
-  for (int q = threadIdx.x; q < kBwdPts * 64; q += blockDim.x) {
-    const int p = q >> 6, k = q & 63;
-    float s = 0.f;
-    if (h1[p][k] > 0.f)
-      for (int j = 0; j < 64; ++j) s += dz2[p][j] * params[kOffW2 + k * 64 + j];
-    dz1[p][k] = s;
-  }
-  __syncthreads();
-  float* out = part + (int64_t)blockIdx.x * kNParams;
-  // dW2[k][j] = sum_p h1[p][k] dz2[p][j]
-  for (int q = threadIdx.x; q < 64 * 64; q += blockDim.x) {
-    const int k = q >> 6, j = q & 63;
-    float s = 0.f;
-    for (int p = 0; p < kBwdPts; ++p) s += h1[p][k] * dz2[p][j];
-    out[kOffW2 + q] = s;
-  }
-  // dW1[f][k] = sum_p x[p][f] dz1[p][k]  (row 31 is the zero feature)
-  for (int q = threadIdx.x; q < 32 * 64; q += blockDim.x) {
-    const int f = q >> 6, k = q & 63;
-    float s = 0.f;
-    for (int p = 0; p < kBwdPts; ++p) s += x[p][f] * dz1[p][k];
-    out[kOffW1 + q] = s;
-  }
-  if (threadIdx.x < 64) {
-    const int j = threadIdx.x;
-    float sb1 = 0.f, sb2 = 0.f, sw3 = 0.f;
-    for (int p = 0; p < kBwdPts; ++p) {
-      sb1 += dz1[p][j];
-      sb2 += dz2[p][j];
-    }
-    // dw3[j] = sum_p dy[p] relu(z2)[p][j]: recomputed from H2 via dz2 / w3 would lose
-    // zeros of w3, so read H2 again
-    for (int p = 0; p < kBwdPts; ++p) {
+  float acc[kBwdPer];
+#pragma unroll
+  for (int e = 0; e < kBwdPer; ++e) acc[e] = 0.f;
+  const int64_t ngroups = ((int64_t)nB + kBwdPts - 1) / kBwdPts;
+  for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
+    const int64_t p0 = grp * kBwdPts;
+    for (int q = threadIdx.x; q < kBwdPts * 64; q += blockDim.x) {
+      const int p = q >> 6, j = q & 63;
       const int64_t gp = p0 + p;
-      if (gp < nB) sw3 += dys[p] * __bfloat162float(H2[gp * 64 + j]);
+      const bool ok = gp < nB;
+      const float dyv = ok ? dy[gp] : 0.f;
+      const float h2v = ok ? __bfloat162float(H2[gp * 64 + j]) : 0.f;
+      h1[p][j] = ok ? __bfloat162float(H1[gp * 64 + j]) : 0.f;
+      h2[p][j] = h2v;
+      dz2[p][j] = h2v > 0.f ? dyv * params[kOffW3 + j] : 0.f;
+      if (j < 32) x[p][j] = ok ? __bfloat162float(Xs[gp * 32 + j]) : 0.f;
+      if (j == 0) dys[p] = dyv;
     }
-    out[kOffB1 + j] = sb1;
-    out[kOffB2 + j] = sb2;
-    out[kOffW3 + j] = sw3;
+    __syncthreads();
+    // dz1 = (dz2 W2^T) * [h1 > 0]
+    for (int q = threadIdx.x; q < kBwdPts * 64; q += blockDim.x) {
+      const int p = q >> 6, k = q & 63;
+      float s = 0.f;
+      if (h1[p][k] > 0.f)
+        for (int j = 0; j < 64; ++j) s += dz2[p][j] * params[kOffW2 + k * 64 + j];
+      dz1[p][k] = s;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < kBwdPer; ++e) {
+      const int q = threadIdx.x + e * kBwdThreads;
+      float s = 0.f;
+      if (q < kOffB1) {  // dW1[f][k] = sum_p x[p][f] dz1[p][k] (row 31: the zero feature)
+        const int f = q >> 6, k = q & 63;
+        for (int p = 0; p < kBwdPts; ++p) s += x[p][f] * dz1[p][k];
+      } else if (q < kOffW2) {  // db1
+        for (int p = 0; p < kBwdPts; ++p) s += dz1[p][q - kOffB1];
+      } else if (q < kOffB2) {  // dW2[k][j] = sum_p h1[p][k] dz2[p][j]
+        const int k = (q - kOffW2) >> 6, j = (q - kOffW2) & 63;
+        for (int p = 0; p < kBwdPts; ++p) s += h1[p][k] * dz2[p][j];
+      } else if (q < kOffW3) {  // db2
+        for (int p = 0; p < kBwdPts; ++p) s += dz2[p][q - kOffB2];
+      } else if (q < kOffB3) {  // dw3[j] = sum_p dy[p] relu(z2)[p][j]
+        for (int p = 0; p < kBwdPts; ++p) s += dys[p] * h2[p][q - kOffW3];
+      } else if (q == kOffB3) {
+        for (int p = 0; p < kBwdPts; ++p) s += dys[p];
+      }
+      acc[e] += s;
+    }
+    __syncthreads();
   }
-  if (threadIdx.x == 64) {
-    float s = 0.f;
-    for (int p = 0; p < kBwdPts; ++p) s += dys[p];
-    out[kOffB3] = s;
+  float* out = part + (int64_t)blockIdx.x * kNParams;
+#pragma unroll
+  for (int e = 0; e < kBwdPer; ++e) {
+    const int q = threadIdx.x + e * kBwdThreads;
+    if (q < kNParams) out[q] = acc[e];
   }
 }
 
@@ -482,7 +487,7 @@ void mlp_forward(const float* params, const MlpLevelData& D, const float* r, flo
 }
 
 void MlpTrainBuffers::ensure(int32_t nB, int64_t nplus) {
-  nparts = (int)((nB + kBwdPts - 1) / kBwdPts);
+  nparts = kBwdCtas;
   if (nB <= n && nplus <= np) return;  // capacity suffices
   n = nB;
   np = nplus;
@@ -497,7 +502,7 @@ void MlpTrainBuffers::ensure(int32_t nB, int64_t nplus) {
   t.alloc(nplus);
   et.alloc(nB);
   dy.alloc(nB);
-  nparts = (int)((nB + kBwdPts - 1) / kBwdPts);
+  nparts = kBwdCtas;
   part.alloc((size_t)nparts * kNParams);
   lpart.alloc(2 * (size_t)((nB + 255) / 256));
   loss.alloc(2);

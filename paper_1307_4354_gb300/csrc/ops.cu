@@ -65,41 +65,232 @@ __device__ inline void block_max_sum(double m, double s, double* part) {
 }
 
 // ----------------------------------------------------------------- M stencil
+// Stencil passes on B, one warp per brick (lane l handles nodes l and l + 32
+// of the 4x4x4 brick; in 2-D lanes 0..15 the 16 nodes of a 4x4 brick).  The
+// Laplacian neighbours of a node are found by brick addressing: a neighbour
+// inside the brick is a local position of the same brick, one across a face
+// is a local position of the face-neighbour brick, and its index in B+ is
+// start + popcount of the occupancy mask below it (band mask first, then
+// ghost mask).  The brick tables are warp-uniform loads, so the pass reads
+// no per-point index table: per point only u, f, diag and w (and writes the
+// result).
+// Occupancy masks and starts of one slot of a brick record.
+struct SlotTab {
+  uint64_t bm, gm;
+  int32_t bs, gs;
+};
+template <bool BAND_ONLY>
+__device__ __forceinline__ SlotTab slot_tab(const BrickRec* R, int q) {
+  SlotTab t;
+  t.bm = __ldg(&R->bm[q]);
+  t.bs = __ldg(&R->bs[q]);
+  t.gm = BAND_ONLY ? 0ull : __ldg(&R->gm[q]);
+  t.gs = BAND_ONLY ? 0 : __ldg(&R->gs[q]);
+  return t;
+}
+// Index in B+ (or in B only) of local node l of a brick, -1 if absent.
+__device__ __forceinline__ int32_t tab_index(const SlotTab& t, int l, int32_t nB) {
+  const uint64_t bit = 1ull << l;
+  if (t.bm & bit) return t.bs + __popcll(t.bm & (bit - 1ull));
+  if (t.gm & bit) return nB + t.gs + __popcll(t.gm & (bit - 1ull));
+  return -1;
+}
+// The 2d neighbours (-x, +x, -y, +y, -z, +z) of local node l: inside the
+// brick (its own tables, already in registers) or across a face (the tables
+// of record slot q + 1, loaded only for nodes on that face).
+template <int DIM, bool BAND_ONLY>
+__device__ __forceinline__ void brick_neighbours(const BrickRec* R, const SlotTab& own, int l,
+                                                 int32_t nB, int32_t k[6]) {
+  const int x = l & 3, y = (l >> 2) & 3, z = l >> 4;
+  const int step[3] = {1, 4, 16};
+  const int pos[3] = {x, y, z};
+#pragma unroll
+  for (int q = 0; q < 2 * DIM; ++q) {
+    const int a = q >> 1;
+    const bool up = q & 1;
+    const bool face = up ? pos[a] == 3 : pos[a] == 0;
+    const int ln = face ? (up ? l - 3 * step[a] : l + 3 * step[a]) : (up ? l + step[a] : l - step[a]);
+    k[q] = tab_index(face ? slot_tab<BAND_ONLY>(R, q + 1) : own, ln, nB);
+  }
+}
+
+// Threads per brick of the stencil passes: 64 (one node each) or 32 (two).
+#ifndef CPM_LAP_TPB
+#define CPM_LAP_TPB 64
+#endif
+constexpr int kLapTPB = CPM_LAP_TPB;
+static_assert(kLapTPB == 32 || kLapTPB == 64, "threads per brick");
+
+// Stencil passes over the per-point neighbour table (1) or by brick
+// addressing (0).
+#ifndef CPM_LAP_INDEXED
+#define CPM_LAP_INDEXED 1
+#endif
+constexpr bool kLapIndexed = CPM_LAP_INDEXED != 0;
+
+template <typename T>
+static unsigned lap_grid(const LevelView<T>& L) {
+  return kLapIndexed ? nblk(L.nB, 256) : nblk((int64_t)L.bv.nbricks * kLapTPB, 256);
+}
+int lap_blocks_f64(const LevelView<double>& L) { return (int)lap_grid(L); }
+
+// MODE (LapMode, plus the Ruuth-Merriman pieces):
+//   APPLY : out = M u
+//   RESID : out = f - c u + M u, block partials of max|out|, sum out^2
+//   JACOBI: u += (f - c u + M u) * dA (in place)
+//   RESID_REL: RESID from the relative extension (w = delta, refv)
+//   RM_JAC / RM_RES: band-restricted Laplacian L_B on u (ghost neighbours
+//           dropped): out = u + omega (f - (cI - L_B) u) / (c + gamma), or
+//           out = f - (cI - L_B) u
+constexpr int LAP_RM_JAC = 8, LAP_RM_RES = 9, LAP_BAND = 10, LAP_VARD = 11;
 template <typename T, int DIM, int MODE>
 __global__ void __launch_bounds__(256) k_lap(LevelView<T> L, const T* u, const T* __restrict__ w,
                                              const T* __restrict__ f, const T* __restrict__ cvec,
                                              T cval, const T* __restrict__ dA, T omega, T* out,
                                              T* u_inout, double* part, const T* __restrict__ refv) {
+  constexpr bool RM = MODE == LAP_RM_JAC || MODE == LAP_RM_RES || MODE == LAP_BAND || MODE == LAP_VARD;
+  const int32_t b = (int32_t)((blockIdx.x * blockDim.x + threadIdx.x) / kLapTPB);
+  const int lane = threadIdx.x % kLapTPB;
+  double rm = 0.0, rs = 0.0;
+  const BrickRec* R = L.bv.brec + (b < L.bv.nbricks ? b : 0);
+  const uint64_t bm = b < L.bv.nbricks ? __ldg(&R->bm[0]) : 0ull;
+  if (bm) {
+    const SlotTab own = slot_tab<RM>(R, 0);
+    const int32_t bs = own.bs;
+#pragma unroll
+    for (int h = 0; h < (DIM == 3 ? 64 / kLapTPB : 1); ++h) {
+      const int l = lane + kLapTPB * h;
+      if ((DIM == 2 && l >= 16) || !((bm >> l) & 1ull)) continue;
+      if ((MODE == LAP_JAC_RED || MODE == LAP_JAC_BLACK) &&
+          node_colour_local(l) != (MODE == LAP_JAC_BLACK ? 1 : 0))
+        continue;
+      const int32_t i = bs + __popcll(bm & ((1ull << l) - 1ull));
+      int32_t k[6];
+      brick_neighbours<DIM, RM>(R, own, l, L.nB, k);
+      const T ui = u[i];
+      if (MODE == LAP_VARD) {  // out = L~ u, refv = the diffusion coefficient a
+        const T ai = refv[i];
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < 2 * DIM; ++q)
+          if (k[q] >= 0) s += (T(0.5) * (ai + refv[k[q]])) * (u[k[q]] - ui);
+        out[i] = s * L.inv_h2;
+        continue;
+      }
+      if (RM) {
+        T s = T(0);
+#pragma unroll
+        for (int q = 0; q < 2 * DIM; ++q)
+          if (k[q] >= 0) s += u[k[q]];
+        if (MODE == LAP_BAND) {  // out = L_B u
+          out[i] = s * L.inv_h2 - L.gamma * ui;
+          continue;
+        }
+        const T c = cvec ? cvec[i] : cval;
+        const T diag = c + L.gamma;
+        const T r = f[i] - diag * ui + s * L.inv_h2;
+        out[i] = MODE == LAP_RM_JAC ? ui + omega * r / diag : r;
+        continue;
+      }
+      const T wi = w[i];
+      T s = T(0), Mu;
+      if (MODE == LAP_RESID_REL) {
+        const T ri = refv[i];
+#pragma unroll
+        for (int q = 0; q < 2 * DIM; ++q) {
+          const int32_t kk = k[q] < 0 ? i : k[q];
+          s += (refv[kk] - ri) + (w[kk] - wi);
+        }
+        Mu = s * L.inv_h2 + L.gamma * ((ri - ui) + wi);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 2 * DIM; ++q) s += w[k[q] < 0 ? i : k[q]] - wi;
+        Mu = s * L.inv_h2 + L.gamma * (wi - ui);
+      }
+      if (MODE == LAP_APPLY) {
+        out[i] = Mu;
+      } else {
+        const T c = cvec ? cvec[i] : cval;
+        const T r = f[i] - c * ui + Mu;
+        if (MODE == LAP_RESID || MODE == LAP_RESID_REL) {
+          out[i] = r;
+          rm = fmax(rm, fabs((double)r));
+          rs += (double)r * (double)r;
+        } else {
+          u_inout[i] = ui + r * dA[i];
+        }
+      }
+    }
+  }
+  if ((MODE == LAP_RESID || MODE == LAP_RESID_REL) && part) block_max_sum(rm, rs, part);
+}
+
+// The same passes with one thread per band point and its 2d neighbours read
+// from the per-point index table (B+ indices, the node itself where a
+// neighbour is missing).  Ruuth-Merriman modes drop ghost neighbours.
+template <typename T, int DIM, int MODE>
+__global__ void __launch_bounds__(256) k_lap_idx(LevelView<T> L, const T* u, const T* __restrict__ w,
+                                                 const T* __restrict__ f, const T* __restrict__ cvec,
+                                                 T cval, const T* __restrict__ dA, T omega, T* out,
+                                                 T* u_inout, double* part, const T* __restrict__ refv) {
+  constexpr bool RM = MODE == LAP_RM_JAC || MODE == LAP_RM_RES || MODE == LAP_BAND || MODE == LAP_VARD;
   const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
   double rm = 0.0, rs = 0.0;
-  if (i < L.nB) {
-    const T wi = w[i];
+  bool active = i < L.nB;
+  if (active && (MODE == LAP_JAC_RED || MODE == LAP_JAC_BLACK)) {
+    const uint64_t kk = __ldg(L.key + i);
+    active = ((key_x(kk) + key_y(kk) + (DIM == 3 ? key_z(kk) : 0)) & 1) == (MODE == LAP_JAC_BLACK ? 1 : 0);
+  }
+  if (active) {
+    int32_t k[6];
+#pragma unroll
+    for (int q = 0; q < 2 * DIM; ++q) k[q] = __ldg(L.nbr + (int64_t)q * L.nB + i);
     const T ui = u[i];
-    T s = T(0), Mu;
-    if (MODE == LAP_RESID_REL) {
-      const T ri = refv[i];
+    if (MODE == LAP_VARD) {  // out = L~ u, refv = the diffusion coefficient a
+      const T ai = refv[i];
+      T s = T(0);
 #pragma unroll
-      for (int q = 0; q < 2 * DIM; ++q) {
-        const int32_t k = __ldg(L.nbr + (int64_t)q * L.nB + i);
-        s += (refv[k] - ri) + (w[k] - wi);
-      }
-      Mu = s * L.inv_h2 + L.gamma * ((ri - ui) + wi);
-    } else {
+      for (int q = 0; q < 2 * DIM; ++q)
+        if (k[q] < L.nB && k[q] != i) s += (T(0.5) * (ai + refv[k[q]])) * (u[k[q]] - ui);
+      out[i] = s * L.inv_h2;
+    } else if (RM) {
+      T s = T(0);
 #pragma unroll
-      for (int q = 0; q < 2 * DIM; ++q) s += w[__ldg(L.nbr + (int64_t)q * L.nB + i)] - wi;
-      Mu = s * L.inv_h2 + L.gamma * (wi - ui);
-    }
-    if (MODE == LAP_APPLY) {
-      out[i] = Mu;
-    } else {
-      const T c = cvec ? cvec[i] : cval;
-      const T r = f[i] - c * ui + Mu;
-      if (MODE == LAP_RESID || MODE == LAP_RESID_REL) {
-        out[i] = r;
-        rm = fabs((double)r);
-        rs = (double)r * (double)r;
+      for (int q = 0; q < 2 * DIM; ++q)
+        if (k[q] < L.nB && k[q] != i) s += u[k[q]];
+      if (MODE == LAP_BAND) {
+        out[i] = s * L.inv_h2 - L.gamma * ui;
       } else {
-        u_inout[i] = ui + r * dA[i];
+        const T c = cvec ? cvec[i] : cval;
+        const T diag = c + L.gamma;
+        const T r = f[i] - diag * ui + s * L.inv_h2;
+        out[i] = MODE == LAP_RM_JAC ? ui + omega * r / diag : r;
+      }
+    } else {
+      const T wi = w[i];
+      T s = T(0), Mu;
+      if (MODE == LAP_RESID_REL) {
+        const T ri = refv[i];
+#pragma unroll
+        for (int q = 0; q < 2 * DIM; ++q) s += (refv[k[q]] - ri) + (w[k[q]] - wi);
+        Mu = s * L.inv_h2 + L.gamma * ((ri - ui) + wi);
+      } else {
+#pragma unroll
+        for (int q = 0; q < 2 * DIM; ++q) s += w[k[q]] - wi;
+        Mu = s * L.inv_h2 + L.gamma * (wi - ui);
+      }
+      if (MODE == LAP_APPLY) {
+        out[i] = Mu;
+      } else {
+        const T c = cvec ? cvec[i] : cval;
+        const T r = f[i] - c * ui + Mu;
+        if (MODE == LAP_RESID || MODE == LAP_RESID_REL) {
+          out[i] = r;
+          rm = fabs((double)r);
+          rs = (double)r * (double)r;
+        } else {
+          u_inout[i] = ui + r * dA[i];
+        }
       }
     }
   }
@@ -109,10 +300,25 @@ __global__ void __launch_bounds__(256) k_lap(LevelView<T> L, const T* u, const T
 template <int DIM, int MODE, typename T>
 static void lap_dispatch(const LevelView<T>& L, const T* u, const T* w, const T* f, const T* cvec,
                          T cval, const T* dA, T omega, T* out, T* u_inout, double* part,
-                         cudaStream_t st) {
-  k_lap<T, DIM, MODE><<<nblk(L.nB, 256), 256, 0, st>>>(L, u, w, f, cvec, cval, dA, omega, out,
-                                                         u_inout, part, nullptr);
+                         const T* refv, cudaStream_t st) {
+  if (kLapIndexed)
+    k_lap_idx<T, DIM, MODE><<<lap_grid(L), 256, 0, st>>>(L, u, w, f, cvec, cval, dA, omega, out,
+                                                          u_inout, part, refv);
+  else
+    k_lap<T, DIM, MODE><<<lap_grid(L), 256, 0, st>>>(L, u, w, f, cvec, cval, dA, omega, out, u_inout,
+                                                      part, refv);
   count_launch();
+}
+
+template <int MODE, typename T>
+static void lap_dim(const LevelView<T>& L, const T* u, const T* w, const T* f, const T* cvec, T cval,
+                    const T* dA, T omega, T* out, T* u_inout, double* part, const T* refv,
+                    cudaStream_t st) {
+  if (L.nB <= 0) return;
+  if (L.dim == 3)
+    lap_dispatch<3, MODE>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, refv, st);
+  else
+    lap_dispatch<2, MODE>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, refv, st);
 }
 
 template <typename T>
@@ -120,67 +326,135 @@ void launch_lap(const LevelView<T>& L, LapMode mode, const T* u, const T* w, con
                 const T* cvec, T cval, const T* dA, T omega, T* out, T* u_inout, double* part,
                 int nblocks_part, cudaStream_t st) {
   (void)nblocks_part;
-  if (L.nB <= 0) return;
-  if (L.dim == 3) {
-    if (mode == LAP_APPLY) lap_dispatch<3, LAP_APPLY>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, st);
-    if (mode == LAP_RESID) lap_dispatch<3, LAP_RESID>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, st);
-    if (mode == LAP_JACOBI) lap_dispatch<3, LAP_JACOBI>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, st);
-  } else {
-    if (mode == LAP_APPLY) lap_dispatch<2, LAP_APPLY>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, st);
-    if (mode == LAP_RESID) lap_dispatch<2, LAP_RESID>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, st);
-    if (mode == LAP_JACOBI) lap_dispatch<2, LAP_JACOBI>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, st);
-  }
+  if (mode == LAP_APPLY) lap_dim<LAP_APPLY>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, (const T*)nullptr, st);
+  if (mode == LAP_RESID) lap_dim<LAP_RESID>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, (const T*)nullptr, st);
+  if (mode == LAP_JACOBI) lap_dim<LAP_JACOBI>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, (const T*)nullptr, st);
+  if (mode == LAP_JAC_RED) lap_dim<LAP_JAC_RED>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, (const T*)nullptr, st);
+  if (mode == LAP_JAC_BLACK) lap_dim<LAP_JAC_BLACK>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, (const T*)nullptr, st);
 }
 
 void launch_resid_rel(const LevelView<double>& L, const double* u, const double* delta,
                       const double* refv, const double* f, const double* cvec, double cval,
                       double* r, double* part, cudaStream_t st) {
-  if (L.nB <= 0) return;
-  if (L.dim == 3)
-    k_lap<double, 3, LAP_RESID_REL><<<nblk(L.nB, 256), 256, 0, st>>>(
-        L, u, delta, f, cvec, cval, nullptr, 0.0, r, nullptr, part, refv);
-  else
-    k_lap<double, 2, LAP_RESID_REL><<<nblk(L.nB, 256), 256, 0, st>>>(
-        L, u, delta, f, cvec, cval, nullptr, 0.0, r, nullptr, part, refv);
-  count_launch();
+  lap_dim<LAP_RESID_REL>(L, u, delta, f, cvec, cval, (const double*)nullptr, 0.0, r, (double*)nullptr,
+                         part, refv, st);
 }
 
 // ----------------------------------------------------------------- Ruuth-Merriman
-template <typename T, int DIM, bool JAC>
-__global__ void __launch_bounds__(256) k_rm(LevelView<T> L, const T* __restrict__ u,
-                                            const T* __restrict__ f, const T* __restrict__ cvec,
-                                            T cval, T omega, T* __restrict__ out) {
-  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= L.nB) return;
-  T s = T(0);
-#pragma unroll
-  for (int q = 0; q < 2 * DIM; ++q) {
-    const int32_t j = __ldg(L.nbr + (int64_t)q * L.nB + i);
-    if (j < L.nB) s += u[j];  // band-restricted Laplacian: ghost neighbours dropped
-  }
-  const T c = cvec ? cvec[i] : cval;
-  const T diag = c + L.gamma;
-  const T ui = u[i];
-  const T r = f[i] - diag * ui + s * L.inv_h2;
-  out[i] = JAC ? ui + omega * r / diag : r;
-}
-
 template <typename T>
 void launch_rm_jacobi(const LevelView<T>& L, const T* u, const T* f, const T* cvec, T cval, T omega,
                       T* out, cudaStream_t st) {
-  if (L.dim == 3) k_rm<T, 3, true><<<nblk(L.nB, 256), 256, 0, st>>>(L, u, f, cvec, cval, omega, out);
-  else k_rm<T, 2, true><<<nblk(L.nB, 256), 256, 0, st>>>(L, u, f, cvec, cval, omega, out);
-  count_launch();
+  lap_dim<LAP_RM_JAC>(L, u, (const T*)nullptr, f, cvec, cval, (const T*)nullptr, omega, out,
+                      (T*)nullptr, nullptr, (const T*)nullptr, st);
 }
 template <typename T>
 void launch_rm_resid(const LevelView<T>& L, const T* u, const T* f, const T* cvec, T cval, T* out,
                      cudaStream_t st) {
-  if (L.dim == 3) k_rm<T, 3, false><<<nblk(L.nB, 256), 256, 0, st>>>(L, u, f, cvec, cval, T(0), out);
-  else k_rm<T, 2, false><<<nblk(L.nB, 256), 256, 0, st>>>(L, u, f, cvec, cval, T(0), out);
+  lap_dim<LAP_RM_RES>(L, u, (const T*)nullptr, f, cvec, cval, (const T*)nullptr, T(0), out,
+                      (T*)nullptr, nullptr, (const T*)nullptr, st);
+}
+
+// ----------------------------------------------------------------- paper form
+// The paper's own scheme (Sec. 3.1, Eq. 3.3): M u = E_1 (L_B u) - gamma (u - E_3 u)
+// on B, with L_B the band-restricted 2d+1-point Laplacian, E_1 linear and
+// E_3 cubic interpolation at cp.  Given v = L_B u (launch_lap_band) and
+// w = E_3 u on B (launch_extend over B), one thread per band point gathers v
+// at the 2^d linear-stencil nodes of cp(x_i) (the middle nodes of its cubic
+// stencil, same fractions) through the brick tables.
+template <typename T>
+void launch_lap_band(const LevelView<T>& L, const T* u, T* v, cudaStream_t st) {
+  lap_dim<LAP_BAND>(L, u, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, T(0),
+                    (const T*)nullptr, T(0), v, (T*)nullptr, nullptr, (const T*)nullptr, st);
+}
+
+template <typename T>
+void launch_lap_vard(const LevelView<T>& L, const T* u, const T* a, T* v, cudaStream_t st) {
+  lap_dim<LAP_VARD>(L, u, (const T*)nullptr, (const T*)nullptr, (const T*)nullptr, T(0),
+                    (const T*)nullptr, T(0), v, (T*)nullptr, nullptr, a, st);
+}
+
+template <typename T, int DIM, int MODE>
+__global__ void __launch_bounds__(256) k_paper(LevelView<T> L, const T* u, const T* __restrict__ v,
+                                               const T* __restrict__ w, const T* __restrict__ f,
+                                               const T* __restrict__ cvec, T cval,
+                                               const T* __restrict__ dA, T* out, T* u_inout,
+                                               double* part, const T* __restrict__ avec) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  double rm = 0.0, rs = 0.0;
+  const uint64_t k = i < L.nB ? __ldg(L.key + i) : 0ull;
+  const bool skip = (MODE == LAP_JAC_RED || MODE == LAP_JAC_BLACK) &&
+                    ((key_x(k) + key_y(k) + (DIM == 3 ? key_z(k) : 0)) & 1) != (MODE == LAP_JAC_BLACK ? 1 : 0);
+  if (i < L.nB && !skip) {
+    const int bx = key_x(k) + key_ox(k) + 1, by = key_y(k) + key_oy(k) + 1;
+    const int bz = DIM == 3 ? key_z(k) + key_oz(k) + 1 : 0;
+    const T sx = __ldg(L.fr + i), sy = __ldg(L.fr + L.nplus + i);
+    const T sz = DIM == 3 ? __ldg(L.fr + 2 * L.nplus + i) : T(0);
+    const T wx[2] = {T(1) - sx, sx}, wy[2] = {T(1) - sy, sy}, wz[2] = {T(1) - sz, sz};
+    T e1v = T(0);
+#pragma unroll
+    for (int c = 0; c < (DIM == 3 ? 2 : 1); ++c) {
+      T accy = T(0);
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb) {
+        const int32_t j0 = band_index(L.bv, bx, by + bb, bz + c);
+        const int32_t j1 = band_index(L.bv, bx + 1, by + bb, bz + c);
+        accy += wy[bb] * (wx[0] * v[j0 < 0 ? i : j0] + wx[1] * v[j1 < 0 ? i : j1]);
+      }
+      e1v += (DIM == 3 ? wz[c] : T(1)) * accy;
+    }
+    const T ui = u[i];
+    const T g = avec ? L.gamma * avec[i] : L.gamma;  // side-condition weight gamma a_i
+    const T Mu = e1v - g * (ui - w[i]);
+    if (MODE == LAP_APPLY) {
+      out[i] = Mu;
+    } else {
+      const T cc = cvec ? cvec[i] : cval;
+      const T r = f[i] - cc * ui + Mu;
+      if (MODE == LAP_RESID) {
+        out[i] = r;
+        rm = fabs((double)r);
+        rs = (double)r * (double)r;
+      } else {
+        u_inout[i] = ui + r * dA[i];
+      }
+    }
+  }
+  if (MODE == LAP_RESID && part) block_max_sum(rm, rs, part);
+}
+
+int paper_blocks(const LevelView<double>& L) { return (int)nblk(L.nB, 256); }
+
+template <typename T>
+void launch_paper(const LevelView<T>& L, LapMode mode, const T* u, const T* v, const T* w, const T* f,
+                  const T* cvec, T cval, const T* dA, T* out, T* u_inout, double* part,
+                  const T* avec, cudaStream_t st) {
+  if (L.nB <= 0) return;
+  const unsigned g = nblk(L.nB, 256);
+#define CPM_PAPER(DIM, MODE) \
+  k_paper<T, DIM, MODE><<<g, 256, 0, st>>>(L, u, v, w, f, cvec, cval, dA, out, u_inout, part, avec)
+  if (L.dim == 3) {
+    if (mode == LAP_APPLY) CPM_PAPER(3, LAP_APPLY);
+    else if (mode == LAP_RESID) CPM_PAPER(3, LAP_RESID);
+    else if (mode == LAP_JAC_RED) CPM_PAPER(3, LAP_JAC_RED);
+    else if (mode == LAP_JAC_BLACK) CPM_PAPER(3, LAP_JAC_BLACK);
+    else CPM_PAPER(3, LAP_JACOBI);
+  } else {
+    if (mode == LAP_APPLY) CPM_PAPER(2, LAP_APPLY);
+    else if (mode == LAP_RESID) CPM_PAPER(2, LAP_RESID);
+    else if (mode == LAP_JAC_RED) CPM_PAPER(2, LAP_JAC_RED);
+    else if (mode == LAP_JAC_BLACK) CPM_PAPER(2, LAP_JAC_BLACK);
+    else CPM_PAPER(2, LAP_JACOBI);
+  }
+#undef CPM_PAPER
   count_launch();
 }
 
 // ----------------------------------------------------------------- transfers
+// Closest-point restriction / prolongation (Sec. 4.3): linear interpolation
+// at each target's cp from the 2^d source nodes around it.  The nodes are
+// found from the packed base node through the source brick map and masks
+// (cached loads shared by neighbouring targets), not from a per-target index
+// table.
 template <typename T, int DIM>
 __global__ void __launch_bounds__(256) k_transfer(TransferView<T> tv, const T* __restrict__ src,
                                                   T* __restrict__ dst, bool add) {
@@ -189,6 +463,13 @@ __global__ void __launch_bounds__(256) k_transfer(TransferView<T> tv, const T* _
   const T sx = __ldg(tv.fr + j), sy = __ldg(tv.fr + tv.n + j);
   const T sz = DIM == 3 ? __ldg(tv.fr + 2 * tv.n + j) : T(0);
   const T wx[2] = {T(1) - sx, sx}, wy[2] = {T(1) - sy, sy}, wz[2] = {T(1) - sz, sz};
+  int x = 0, y = 0, z = 0;
+  if (!tv.idx) {
+    const uint64_t kb = __ldg(tv.base + j);
+    x = (int)(kb & 0xffffu);
+    y = (int)((kb >> 16) & 0xffffu);
+    z = (int)((kb >> 32) & 0xffffu);
+  }
   T acc = T(0);
 #pragma unroll
   for (int c = 0; c < (DIM == 3 ? 2 : 1); ++c) {
@@ -196,8 +477,11 @@ __global__ void __launch_bounds__(256) k_transfer(TransferView<T> tv, const T* _
 #pragma unroll
     for (int bb = 0; bb < 2; ++bb) {
       const int q = 4 * c + 2 * bb;
-      const T v0 = __ldg(src + __ldg(tv.src_idx + (int64_t)q * tv.n + j));
-      const T v1 = __ldg(src + __ldg(tv.src_idx + (int64_t)(q + 1) * tv.n + j));
+      const int32_t i0 = tv.idx ? __ldg(tv.idx + (int64_t)q * tv.n + j) : band_index(tv.src, x, y + bb, z + c);
+      const int32_t i1 = tv.idx ? __ldg(tv.idx + (int64_t)(q + 1) * tv.n + j)
+                                : band_index(tv.src, x + 1, y + bb, z + c);
+      const T v0 = __ldg(src + (i0 < 0 ? 0 : i0));
+      const T v1 = __ldg(src + (i1 < 0 ? 0 : i1));
       accy += wy[bb] * (wx[0] * v0 + wx[1] * v1);
     }
     acc += (DIM == 3 ? wz[c] : T(1)) * accy;
@@ -205,11 +489,49 @@ __global__ void __launch_bounds__(256) k_transfer(TransferView<T> tv, const T* _
   dst[j] = add ? dst[j] + acc : acc;
 }
 
+// Cubic restriction / prolongation: degree-3 interpolation at the target's cp
+// from the 4^d source nodes around it (base = floor - 1), tensor-product
+// Lagrange weights, contracted x, then y, then z.
+template <typename T, int DIM>
+__global__ void __launch_bounds__(256) k_transfer3(TransferView<T> tv, const T* __restrict__ src,
+                                                   T* __restrict__ dst, bool add) {
+  const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= tv.n) return;
+  const uint64_t kb = __ldg(tv.base + j);
+  const int x = (int)(kb & 0xffffu), y = (int)((kb >> 16) & 0xffffu), z = (int)((kb >> 32) & 0xffffu);
+  T wx[4], wy[4], wz[4] = {T(1), T(0), T(0), T(0)};
+  cubic_w(__ldg(tv.fr + j), wx);
+  cubic_w(__ldg(tv.fr + tv.n + j), wy);
+  if (DIM == 3) cubic_w(__ldg(tv.fr + 2 * tv.n + j), wz);
+  T acc = T(0);
+#pragma unroll
+  for (int c = 0; c < (DIM == 3 ? 4 : 1); ++c) {
+    T accy = T(0);
+#pragma unroll
+    for (int bb = 0; bb < 4; ++bb) {
+      T accx = T(0);
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int32_t i = band_index(tv.src, x + a, y + bb, z + c);
+        accx += wx[a] * __ldg(src + (i < 0 ? 0 : i));
+      }
+      accy += wy[bb] * accx;
+    }
+    acc += wz[c] * accy;
+  }
+  dst[j] = add ? dst[j] + acc : acc;
+}
+
 template <typename T>
 void launch_transfer(const TransferView<T>& tv, const T* src, T* dst, bool add, cudaStream_t st) {
   if (tv.n <= 0) return;
-  if (tv.dim == 3) k_transfer<T, 3><<<nblk(tv.n, 256), 256, 0, st>>>(tv, src, dst, add);
-  else k_transfer<T, 2><<<nblk(tv.n, 256), 256, 0, st>>>(tv, src, dst, add);
+  if (tv.deg == 3) {
+    if (tv.dim == 3) k_transfer3<T, 3><<<nblk(tv.n, 256), 256, 0, st>>>(tv, src, dst, add);
+    else k_transfer3<T, 2><<<nblk(tv.n, 256), 256, 0, st>>>(tv, src, dst, add);
+  } else {
+    if (tv.dim == 3) k_transfer<T, 3><<<nblk(tv.n, 256), 256, 0, st>>>(tv, src, dst, add);
+    else k_transfer<T, 2><<<nblk(tv.n, 256), 256, 0, st>>>(tv, src, dst, add);
+  }
   count_launch();
 }
 
@@ -353,6 +675,130 @@ void launch_diag_M(const LevelView<double>& L, double* diagM, cudaStream_t st) {
   if (L.dim == 3) k_diag_M<3><<<nblk(L.nB, 256), 256, 0, st>>>(L, diagM);
   else k_diag_M<2><<<nblk(L.nB, 256), 256, 0, st>>>(L, diagM);
 }
+
+// ----------------------------------------------------------------- setup: paper form
+// diag(M_p)_ii = sum_j (E_1)_ij (L_B)_ji - gamma (1 - (E_3)_ii): over the 2^d
+// linear-stencil nodes j of cp(x_i), (L_B)_ji is -2d/dx^2 for j = i and
+// 1/dx^2 for a Laplacian neighbour j of i; (E_3)_ii is the cubic weight of
+// node i in its own stencil (0 if it lies outside).
+// Variable diffusion (a != null): (L~)_ji = (a_j + a_i) / (2 dx^2) for a
+// Laplacian neighbour j of i in B, (L~)_ii = -sum over the neighbours k of i
+// in B of (a_i + a_k) / (2 dx^2), and the side condition is weighted by
+// gamma a_i.
+__device__ __forceinline__ double vard_ii(const LevelView<double>& L, const double* a, int x, int y,
+                                          int z, int dim, int32_t i) {
+  const int d[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  double s = 0.0;
+  for (int q = 0; q < 2 * dim; ++q) {
+    const int32_t k = band_index(L.bv, x + d[q][0], y + d[q][1], z + d[q][2]);
+    if (k >= 0) s -= 0.5 * (a[i] + a[k]) * L.inv_h2;
+  }
+  return s;
+}
+
+template <int DIM>
+__global__ void k_diag_Mp(LevelView<double> L, double* __restrict__ diagM, const double* __restrict__ acoef) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= L.nB) return;
+  const uint64_t k = L.key[i];
+  const int own[3] = {key_x(k), key_y(k), key_z(k)};
+  const int b3[3] = {key_x(k) + key_ox(k), key_y(k) + key_oy(k), key_z(k) + key_oz(k)};
+  double s[3], w3[3][4];
+  for (int a = 0; a < DIM; ++a) {
+    s[a] = L.fr[a * L.nplus + i];
+    cubic_w(s[a], w3[a]);
+  }
+  double e1l = 0.0;
+  for (int c = 0; c < (DIM == 3 ? 2 : 1); ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        const int j[3] = {b3[0] + 1 + a, b3[1] + 1 + b, DIM == 3 ? b3[2] + 1 + c : 0};
+        const double w1 = (a ? s[0] : 1.0 - s[0]) * (b ? s[1] : 1.0 - s[1]) *
+                          (DIM == 3 ? (c ? s[2] : 1.0 - s[2]) : 1.0);
+        int dist = 0;
+        for (int q = 0; q < DIM; ++q) dist += abs(j[q] - own[q]);
+        if (!acoef) {
+          if (dist == 0) e1l += w1 * (-L.gamma);
+          else if (dist == 1) e1l += w1 * L.inv_h2;
+        } else if (dist == 0) {
+          e1l += w1 * vard_ii(L, acoef, own[0], own[1], own[2], DIM, i);
+        } else if (dist == 1) {
+          const int32_t jj = band_index(L.bv, j[0], j[1], j[2]);
+          if (jj >= 0) e1l += w1 * 0.5 * (acoef[jj] + acoef[i]) * L.inv_h2;
+        }
+      }
+  double e3 = 1.0;
+  for (int q = 0; q < DIM; ++q) {
+    const int off = own[q] - b3[q];
+    e3 = (off < 0 || off > 3) ? 0.0 : e3 * w3[q][off];
+  }
+  diagM[i] = e1l - (acoef ? L.gamma * acoef[i] : L.gamma) * (1.0 - e3);
+}
+
+void launch_diag_Mp(const LevelView<double>& L, double* diagM, const double* a, cudaStream_t st) {
+  if (L.dim == 3) k_diag_Mp<3><<<nblk(L.nB, 256), 256, 0, st>>>(L, diagM, a);
+  else k_diag_Mp<2><<<nblk(L.nB, 256), 256, 0, st>>>(L, diagM, a);
+}
+
+// Row i of A_p = cI - M_p = (c + gamma) I - E_1 L_B - gamma E_3.  One thread per row.
+template <int DIM, typename M>
+__global__ void k_assemble_Ap(LevelView<double> L, const double* cvec, double cval, M* A,
+                              const double* acoef) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int32_t n = L.nB;
+  if (i >= n) return;
+  M* row = A + (size_t)i * n;
+  const double gi = acoef ? L.gamma * acoef[i] : L.gamma;
+  row[i] += (M)((cvec ? cvec[i] : cval) + gi);
+  const uint64_t k = L.key[i];
+  const int b3[3] = {key_x(k) + key_ox(k), key_y(k) + key_oy(k), key_z(k) + key_oz(k)};
+  double s[3] = {0.0, 0.0, 0.0}, w3[3][4] = {{1.0, 0.0, 0.0, 0.0}, {1.0, 0.0, 0.0, 0.0}, {1.0, 0.0, 0.0, 0.0}};
+  for (int a = 0; a < DIM; ++a) {
+    s[a] = L.fr[a * L.nplus + i];
+    cubic_w(s[a], w3[a]);
+  }
+  for (int c = 0; c < (DIM == 3 ? 4 : 1); ++c)
+    for (int b = 0; b < 4; ++b)
+      for (int a = 0; a < 4; ++a) {
+        const int32_t j = band_index(L.bv, b3[0] + a, b3[1] + b, DIM == 3 ? b3[2] + c : 0);
+        if (j >= 0) row[j] -= (M)(gi * w3[0][a] * w3[1][b] * w3[2][c]);
+      }
+  const int d[6][3] = {{-1, 0, 0}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0}, {0, 0, -1}, {0, 0, 1}};
+  for (int c = 0; c < (DIM == 3 ? 2 : 1); ++c)
+    for (int b = 0; b < 2; ++b)
+      for (int a = 0; a < 2; ++a) {
+        const int jx = b3[0] + 1 + a, jy = b3[1] + 1 + b, jz = DIM == 3 ? b3[2] + 1 + c : 0;
+        const double w1 = (a ? s[0] : 1.0 - s[0]) * (b ? s[1] : 1.0 - s[1]) *
+                          (DIM == 3 ? (c ? s[2] : 1.0 - s[2]) : 1.0);
+        const int32_t jj = band_index(L.bv, jx, jy, jz);
+        if (!acoef) {
+          if (jj >= 0) row[jj] -= (M)(w1 * -L.gamma);
+          for (int q = 0; q < 2 * DIM; ++q) {
+            const int32_t kk = band_index(L.bv, jx + d[q][0], jy + d[q][1], jz + d[q][2]);
+            if (kk >= 0) row[kk] -= (M)(w1 * L.inv_h2);
+          }
+        } else if (jj >= 0) {  // row jj of L~ (its own band-restricted neighbours)
+          for (int q = 0; q < 2 * DIM; ++q) {
+            const int32_t kk = band_index(L.bv, jx + d[q][0], jy + d[q][1], jz + d[q][2]);
+            if (kk < 0) continue;
+            const double face = 0.5 * (acoef[jj] + acoef[kk]) * L.inv_h2;
+            row[kk] -= (M)(w1 * face);
+            row[jj] += (M)(w1 * face);
+          }
+        }
+      }
+}
+
+template <typename M>
+void launch_assemble_Ap(const LevelView<double>& L, const double* cvec, double cval, M* A,
+                        const double* a, cudaStream_t st) {
+  if (L.dim == 3) k_assemble_Ap<3, M><<<nblk(L.nB, 128), 128, 0, st>>>(L, cvec, cval, A, a);
+  else k_assemble_Ap<2, M><<<nblk(L.nB, 128), 128, 0, st>>>(L, cvec, cval, A, a);
+}
+template void launch_assemble_Ap<double>(const LevelView<double>&, const double*, double, double*,
+                                         const double*, cudaStream_t);
+template void launch_assemble_Ap<float>(const LevelView<double>&, const double*, double, float*,
+                                        const double*, cudaStream_t);
 
 // ----------------------------------------------------------------- setup: dense A
 // Row i of A = diag(c) - M: A_ii += c_i + gamma, A_ij -= E_{k,j}/dx^2 for each
@@ -508,6 +954,11 @@ void invert_dense(double* A, int32_t n, cudaStream_t st, int32_t* err) {
   template void launch_rm_resid<T>(const LevelView<T>&, const T*, const T*, const T*, T, T*,     \
                                    cudaStream_t);                                                \
   template void launch_transfer<T>(const TransferView<T>&, const T*, T*, bool, cudaStream_t);    \
+  template void launch_lap_band<T>(const LevelView<T>&, const T*, T*, cudaStream_t);            \
+  template void launch_paper<T>(const LevelView<T>&, LapMode, const T*, const T*, const T*,     \
+                                const T*, const T*, T, const T*, T*, T*, double*, const T*,      \
+                                cudaStream_t);                                                   \
+  template void launch_lap_vard<T>(const LevelView<T>&, const T*, const T*, T*, cudaStream_t);  \
   template void launch_norm_partials<T>(const T*, int64_t, double*, cudaStream_t);               \
   template void launch_cast_to_f64<T>(const T*, double*, int64_t, cudaStream_t);                 \
   template void launch_cast_from_f64<T>(const double*, T*, int64_t, cudaStream_t);               \

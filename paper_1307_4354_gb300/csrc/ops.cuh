@@ -28,20 +28,33 @@ struct LevelView {
   const float* efr;     // E-order FP32 fractions
   const double* ew64;   // E-order FP64 weights
   int32_t ntiles;
+  const uint32_t* echunk;     // chunk records (ext.cu)
+  const int32_t* tile_cstart; // ntiles + 1 chunk offsets
+  const int32_t* tile_cmid;   // per tile: end of its chunks of B
   const int32_t* nbr;   // 2d x nB neighbour indices into B+
 };
 
 // Transfer records: for each target point, the base node of its linear
-// (2^d) stencil in the source grid and the fractions (SoA, d x n).
+// (2^d) or cubic (4^d) stencil in the source grid (packed x | y << 16 | z << 32)
+// and the fractions (SoA, d x n).  The stencil nodes are located through the source
+// level's brick tables.
 template <typename T>
 struct TransferView {
-  const int32_t* src_idx;  // 2^d x n band indices of the stencil nodes in the source level
+  const uint64_t* base;    // n packed base nodes in the source grid
   const T* fr;
+  BrickView src;           // brick tables of the source level
   int32_t n;               // number of target points
   int dim;
+  int deg;                 // 1: linear (2^d nodes from base), 3: cubic (4^d nodes)
+  const int32_t* idx;      // linear: 2^d x n source band indices, or null (brick lookups)
 };
 
-enum LapMode { LAP_APPLY = 0, LAP_RESID = 1, LAP_JACOBI = 2, LAP_RESID_REL = 3 };
+enum LapMode { LAP_APPLY = 0, LAP_RESID = 1, LAP_JACOBI = 2, LAP_RESID_REL = 3,
+               LAP_JAC_RED = 4, LAP_JAC_BLACK = 5 };  // Jacobi update of one colour only
+// Red (0) / black (1): parity of the sum of the grid coordinates.  Bricks start
+// at multiples of 4, so the parity of the local coordinates inside a brick is
+// that of the global ones.
+__host__ __device__ inline int node_colour_local(int l) { return ((l & 3) + ((l >> 2) & 3) + (l >> 4)) & 1; }
 
 // w = E u on the first npts points of B+ (npts = nB or nB + nG).
 template <typename T>
@@ -69,6 +82,33 @@ template <typename T>
 void launch_lap(const LevelView<T>& L, LapMode mode, const T* u, const T* w, const T* f,
                 const T* cvec, T cval, const T* dA, T omega, T* out, T* u_inout, double* part,
                 int nblocks_part, cudaStream_t st);
+
+// Number of blocks (2 partial doubles each) of a RESID / RESID_REL stencil pass.
+int lap_blocks_f64(const LevelView<double>& L);
+
+// The paper's scheme M_p u = E_1 (L_B u) - gamma (u - E_3 u) (Eq. 3.3):
+// v = L_B u on B (band-restricted Laplacian); then, with w = E_3 u on B,
+//   APPLY : out = M_p u
+//   RESID : out = f - c u + M_p u (block partials into part, paper_blocks blocks)
+//   JACOBI: u += (f - c u + M_p u) dA (in place)
+template <typename T>
+void launch_lap_band(const LevelView<T>& L, const T* u, T* v, cudaStream_t st);
+// avec != null: the variable-diffusion form (Sec. 4.5.6) E_1 L~ - diag(gamma a)
+// (I - E_3), v = L~ u from launch_lap_vard.
+template <typename T>
+void launch_paper(const LevelView<T>& L, LapMode mode, const T* u, const T* v, const T* w, const T* f,
+                  const T* cvec, T cval, const T* dA, T* out, T* u_inout, double* part,
+                  const T* avec, cudaStream_t st);
+// v = L~ u = sum over axes of D^b diag(A^f a) D^f u on B (band-restricted).
+template <typename T>
+void launch_lap_vard(const LevelView<T>& L, const T* u, const T* a, T* v, cudaStream_t st);
+int paper_blocks(const LevelView<double>& L);
+// diag(M_p) and the dense A_p = cI - M_p (setup, FP64 records); a != null:
+// the variable-diffusion form.
+void launch_diag_Mp(const LevelView<double>& L, double* diagM, const double* a, cudaStream_t st);
+template <typename M>
+void launch_assemble_Ap(const LevelView<double>& L, const double* cvec, double cval, M* A,
+                        const double* a, cudaStream_t st);
 
 // RM smoother pieces: u += omega (f - (cI - L_B) u) / (c + gamma) with the
 // band-restricted Laplacian, written to out (out may not alias u).

@@ -12,8 +12,8 @@ import torch
 from . import capi
 
 _KINDS = {"circle": capi.CPM_CIRCLE, "sphere": capi.CPM_SPHERE, "torus": capi.CPM_TORUS,
-          "ellipsoid": capi.CPM_ELLIPSOID}
-_SMOOTHERS = {"jacobi": capi.CPM_SMOOTH_JACOBI, "rm": capi.CPM_SMOOTH_RM}
+          "ellipsoid": capi.CPM_ELLIPSOID, "dziuk": capi.CPM_DZIUK}
+_SMOOTHERS = {"jacobi": capi.CPM_SMOOTH_JACOBI, "rm": capi.CPM_SMOOTH_RM, "rbgs": capi.CPM_SMOOTH_RBGS}
 
 
 def make_surface(kind: str, *params: float) -> capi.cpm_surface:
@@ -64,6 +64,10 @@ class Band:
         capi.cpm_band_export(self.handle, ijk.ctypes.data, cp.ctypes.data, base.ctypes.data)
         return ijk, cp, base
 
+    def counts(self, stream=None):
+        """(|B|, nnz(L), nnz(E_3), nnz(M)) as Table 4.1 counts them (cpm_band_counts)."""
+        return tuple(capi.cpm_band_counts(self.handle, _stream(stream)))
+
     def close(self):
         if getattr(self, "handle", None):
             capi.cpm_band_destroy(self.handle)
@@ -83,13 +87,18 @@ class Hierarchy:
                  omega: float = 0.8, smoother: str = "jacobi", c: float = 1.0,
                  c_device: torch.Tensor | None = None, residual: str = "extended",
                  coarse_sweeps: int = 0, coarse_f64_max: int = 0, coarse_dense_max: int = 0,
-                 stream=None):
+                 op_form: str = "mbr", transfer_deg: int = 1, cycle: int = 1,
+                 a_device: torch.Tensor | None = None, stream=None):
         o = capi.cpm_mg_opts()
         o.coarsest_dx, o.nu1, o.nu2, o.omega = coarsest_dx, nu1, nu2, omega
-        o.smoother, o.transfer_deg, o.c = _SMOOTHERS[smoother], 1, c
+        o.smoother, o.transfer_deg, o.c = _SMOOTHERS[smoother], transfer_deg, c
+        o.cycle = cycle
         o.residual_mode = {"extended": capi.CPM_RESID_EXTENDED, "plain": capi.CPM_RESID_PLAIN}[residual]
         o.coarse_sweeps = coarse_sweeps
         o.coarse_f64_max, o.coarse_dense_max = coarse_f64_max, coarse_dense_max
+        o.op_form = {"mbr": capi.CPM_OP_MBR, "paper": capi.CPM_OP_PAPER,
+                     "vardiff": capi.CPM_OP_VARDIFF}[op_form]
+        o.a_device = _ptr(a_device, torch.float64, band.nb) if a_device is not None else None
         o.c_device = _ptr(c_device, torch.float64, band.nb) if c_device is not None else None
         self.band = band
         self.handle = capi.cpm_build_hierarchy(band.handle, o, _stream(stream))
@@ -166,7 +175,7 @@ class Hierarchy:
     def solve(self, f: torch.Tensor, u: torch.Tensor | None = None, tol: float = 1e-10,
               max_iter: int = 100, mode: str = "f64", use_graph: bool = True, stream=None,
               raise_on_fail: bool = True, inner_cycles: int = 1, zero_init: bool | None = None,
-              learned: bool = False):
+              learned: bool = False, fmg: bool = False):
         zero = u is None if zero_init is None else bool(zero_init)
         if u is None:
             u = torch.empty_like(f)
@@ -176,6 +185,7 @@ class Hierarchy:
         o.use_graph, o.zero_init = int(use_graph), int(zero)
         o.inner_cycles = inner_cycles
         o.learned = int(learned)
+        o.fmg = int(fmg)
         st, rep = capi.cpm_solve(self.handle, _ptr(f, torch.float64, self.nb),
                                  _ptr(u, torch.float64, self.nb), o, _stream(stream), raise_on_fail)
         n = min(rep.iters + 1, capi.CPM_MAX_HISTORY)
@@ -257,10 +267,30 @@ class Batch:
 class Smoother:
     """Learned smoother network (cpm_mlp): parameters live on the device."""
 
-    def __init__(self, seed: int = 0, params: np.ndarray | None = None):
-        self.handle = capi.cpm_mlp_create(seed)
+    def __init__(self, seed: int = 0, params: np.ndarray | None = None, handle: int | None = None):
+        self.handle = handle if handle is not None else capi.cpm_mlp_create(seed)
         if params is not None:
             self.set_params(params)
+
+    @classmethod
+    def load(cls, path: str) -> "Smoother":
+        """A network written by ``save`` (cpm_mlp_load)."""
+        return cls(handle=capi.cpm_mlp_load(path))
+
+    def train(self, fields, steps: int = 400, lr: float = 2e-3, lr_final: float = 0.0,
+              reset: bool = False, stream=None) -> dict:
+        """cpm_mlp_train on [(Hierarchy, FP64 residual field), ...]; the library
+        scales each field, sets this network as the hierarchies' smoother and
+        runs the Adam schedule."""
+        o = capi.cpm_train_opts()
+        o.steps, o.lr, o.lr_final, o.reset = steps, lr, lr_final, int(reset)
+        hs = [h.handle for h, _ in fields]
+        rs = [_ptr(r, torch.float64, h.nb) for h, r in fields]
+        for h, _ in fields:
+            h._smoother = self
+        rep = capi.cpm_mlp_train(self.handle, hs, rs, o, _stream(stream))
+        return {"steps": rep.steps, "fields": rep.n_fields, "loss_first": rep.loss_first,
+                "loss_last": rep.loss_last, "seconds": rep.seconds}
 
     def get_params(self) -> np.ndarray:
         out = np.empty(capi.CPM_MLP_NPARAMS, np.float32)
@@ -273,7 +303,8 @@ class Smoother:
         capi.cpm_mlp_set_params(self.handle, p.ctypes.data)
 
     def save(self, path: str):
-        np.save(path, self.get_params())
+        """Parameters and Adam state to a file (cpm_mlp_save)."""
+        capi.cpm_mlp_save(self.handle, path)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -1,11 +1,12 @@
-"""Training of the learned smoother on residuals of the method's own V-cycles.
+"""Training data for the learned smoother: residuals of the method's own V-cycles.
 
-Residual fields come from mixed-precision solves on seeded surfaces: for a
-right-hand side f, the outer residuals r_k = f - A u_k of the first few outer
-iterations (the inputs the smoother sees at the start of a V-cycle) are
-computed with the library (cpm_solve with a capped iteration count, then
-cpm_residual) and cast to FP32.  Each training step is one Adam step of the
-library's own forward/backward kernels on one field (cpm_mlp_train_step).
+For a right-hand side f on a seeded surface, the outer residuals
+r_k = f - A u_k of the first few outer iterations of a mixed-precision solve
+(the inputs the smoother sees at the start of a V-cycle) are produced with the
+library (cpm_solve with a capped iteration count, then cpm_residual).  The
+fields stay FP64 on the device; ``Smoother.train`` (cpm_mlp_train) scales and
+casts them and runs the Adam schedule inside the library.  Nothing here
+computes: it only chooses surfaces and calls the C ABI.
 """
 from __future__ import annotations
 
@@ -16,7 +17,7 @@ import torch
 
 import synth
 
-from .solver import Band, Hierarchy, Smoother
+from .solver import Band, Hierarchy
 
 
 def training_surfaces(seed: int = 0, n_ellipsoids: int = 3, n_tori: int = 2):
@@ -36,7 +37,7 @@ def _coarsest(kind, params, dx):
 
 
 def residual_fields(kind, params, dx, seed, iters=(0, 1, 2, 3), c_fn=None):
-    """(hierarchy, [FP32 residual fields]) for one surface and one random f."""
+    """(hierarchy, [FP64 residual fields on the device]) for one surface and one random f."""
     band = Band(kind, params, dx)
     _, cp, _ = band.export()
     cpb = cp[: band.nb]
@@ -55,32 +56,22 @@ def residual_fields(kind, params, dx, seed, iters=(0, 1, 2, 3), c_fn=None):
             u, _ = H.solve(ft, tol=1e-14, max_iter=k, mode="mixed", inner_cycles=1,
                            raise_on_fail=False)
             r = H.residual(ft, u)
-        fields.append((r / r.abs().max()).float().contiguous())
+        fields.append(r)
     H._f = ft
     return H, fields
 
 
-def train(smoother: Smoother, sets, steps: int = 400, lr: float = 2e-3, log_every: int = 0):
-    """Adam steps cycling over the (hierarchy, fields) sets; returns the loss history."""
-    hist = []
-    for H, _ in sets:
-        H.set_smoother(smoother)
-    per = max(1, steps // max(1, sum(len(f) for _, f in sets)))
-    step = 0
-    while step < steps:
-        for H, fields in sets:
-            for r in fields:
-                for _ in range(per):
-                    if step >= steps:
-                        break
-                    want = log_every and step % log_every == 0
-                    loss = H.smoother_train_step(r, lr, want_loss=bool(want))
-                    if want:
-                        hist.append((step, loss))
-                    step += 1
-    return hist
+def training_set(seed: int = 0, spacings=(1 / 64, 1 / 96, 1 / 128), n_ellipsoids: int = 3,
+                 n_tori: int = 2, iters=(0, 1, 2, 3)):
+    """Residual fields of seeded ellipsoids and tori, each at a spacing drawn in turn
+    from `spacings` (the training spacings of the learned-smoother workload)."""
+    sets = []
+    for i, (kind, prm) in enumerate(training_surfaces(seed, n_ellipsoids, n_tori)):
+        sets.append(residual_fields(kind, prm, spacings[i % len(spacings)], seed=seed + i, iters=iters))
+    return sets
 
 
-def mean_loss(sets) -> float:
-    vals = [H.smoother_loss_grad(r)[0] for H, fields in sets for r in fields]
-    return float(np.mean(vals))
+def train(smoother, sets, steps: int = 400, lr: float = 2e-3, lr_final: float = 0.0) -> dict:
+    """cpm_mlp_train over every field of every (hierarchy, fields) set."""
+    pairs = [(H, r) for H, fields in sets for r in fields]
+    return smoother.train(pairs, steps=steps, lr=lr, lr_final=lr_final)

@@ -174,3 +174,40 @@ def harmonic_fields(y: np.ndarray, seeds, degrees=SPHERE_DEGREES) -> list[np.nda
     lm = [(l, m) for l in degrees for m in range(-l, l + 1)]
     Y = np.stack([real_sph_harm(l, m, d) for l, m in lm], axis=1)
     return [Y @ np.array([a for _, _, a in sphere_coefficients(s, degrees)]) for s in seeds]
+
+
+def sphere_vardiff(y: np.ndarray, c=1.0):
+    """Variable-diffusion example on the unit sphere (Sec. 4.5.6): with the polar
+    angle phi (cos phi = z), u = cos phi, a = cos phi + 1.5 and
+    f = 2 cos phi (cos phi + 1.5) - sin^2 phi + c u.  Returns (u, a, f) at y."""
+    z = y[:, 2] / np.linalg.norm(y, axis=1)
+    u = z
+    a = z + 1.5
+    f = 2.0 * z * (z + 1.5) - (1.0 - z * z) + c * u
+    return u, a, f
+
+
+def dziuk_rhs(y: np.ndarray, c=1.0):
+    """Exact solution u = x1 x2 on the Dziuk surface (x1 - x3^2)^2 + x2^2 + x3^2 = 1
+    and f = -Lap_S u + c u at points y of the surface (Sec. 4.5.5).  With
+    n = g / |g|, g = (a, x2, x3 (1 - 2a)), a = x1 - x3^2 and p = grad u =
+    (x2, x1, 0): Lap_S u = -2 n1 n2 - (p.n) div(n), where
+    div(n) = div(g) / |g| - g.grad(|g|^2) / (2 |g|^3), div(g) = 3 - 2a + 4 x3^2.
+    Returns (u, f)."""
+    x1, x2, x3 = y[:, 0], y[:, 1], y[:, 2]
+    a = x1 - x3 * x3
+    g = np.stack([a, x2, x3 * (1.0 - 2.0 * a)], axis=1)
+    s2 = (g * g).sum(axis=1)
+    s = np.sqrt(s2)
+    n = g / s[:, None]
+    # gradient of |g|^2 = a^2 + x2^2 + x3^2 (1 - 2a)^2
+    ds1 = 2.0 * a - 4.0 * x3 * x3 * (1.0 - 2.0 * a)
+    ds2 = 2.0 * x2
+    ds3 = -4.0 * a * x3 + 2.0 * x3 * (1.0 - 2.0 * a) ** 2 + 8.0 * x3 ** 3 * (1.0 - 2.0 * a)
+    div_g = 3.0 - 2.0 * a + 4.0 * x3 * x3
+    div_n = div_g / s - (g[:, 0] * ds1 + g[:, 1] * ds2 + g[:, 2] * ds3) / (2.0 * s2 * s)
+    pn = x2 * n[:, 0] + x1 * n[:, 1]
+    u = x1 * x2
+    lap = -2.0 * n[:, 0] * n[:, 1] - pn * div_n
+    return u, -lap + c * u
+

@@ -2,14 +2,15 @@
 import numpy as np
 import pytest
 
-from oracle.geometry import circle, ellipsoid, sphere, torus
+from oracle.geometry import circle, dziuk, ellipsoid, sphere, torus
 
 
 def oracle_surface(kind, params):
     return {"circle": lambda: circle(*params) if params else circle(),
             "sphere": lambda: sphere(*params) if params else sphere(),
             "torus": lambda: torus(*params),
-            "ellipsoid": lambda: ellipsoid(*params)}[kind]()
+            "ellipsoid": lambda: ellipsoid(*params),
+            "dziuk": dziuk}[kind]()
 
 
 def gpu_keys(ijk, n):

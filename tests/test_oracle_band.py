@@ -109,3 +109,45 @@ def test_ellipsoid_medial_disk_is_far():
     Y = np.stack([1.1 * np.sin(ph) * np.cos(th), 0.8 * np.sin(ph) * np.sin(th), 0.7 * np.cos(ph)], -1).reshape(-1, 3)
     for x in X:
         assert np.sqrt(((Y - x) ** 2).sum(1)).min() >= surf.reach * 0.99
+
+
+def _dziuk_surface_points(n=60, seed=0):
+    rng = np.random.default_rng(seed)
+    z = rng.uniform(-0.99, 0.99, n * n)
+    t = rng.uniform(0, 2 * np.pi, n * n)
+    rho = np.sqrt(1 - z * z)
+    return np.stack([z * z + rho * np.cos(t), rho * np.sin(t), z], 1)
+
+
+def _dziuk_normal(P):
+    a = P[:, 0] - P[:, 2] ** 2
+    g = np.stack([a, P[:, 1], P[:, 2] * (1 - 2 * a)], 1)
+    return g / np.linalg.norm(g, axis=1, keepdims=True)
+
+
+def test_dziuk_closest_point_by_newton():
+    """Sec. 4.5.5: points x = y + t n(y) off the Dziuk surface with |t| below the
+    reach return cp(x) = y (the foot of the normal), on the surface, and dist2
+    = t^2; the reach is the smallest radius of curvature (1 / 10.44)."""
+    from oracle.geometry import DZIUK_REACH, _dziuk, dziuk_min_curvature_radius
+    assert abs(dziuk_min_curvature_radius() - DZIUK_REACH) < 1e-3
+    P = _dziuk_surface_points()
+    nrm = _dziuk_normal(P)
+    t = np.random.default_rng(1).uniform(-0.9, 0.9, len(P)) * DZIUK_REACH
+    X = P + t[:, None] * nrm
+    cp, d2 = _dziuk(X)
+    assert np.abs(cp - P).max() < 1e-9
+    assert np.abs(np.sqrt(d2) - np.abs(t)).max() < 1e-9
+
+
+def test_dziuk_candidate_filter_keeps_the_tube():
+    """The oracle's candidate filter (first-order distance with slack) keeps
+    every point within 2 band half-widths of the surface at dx = 1/64."""
+    from oracle.band import _candidate_filter
+    from oracle.geometry import dziuk
+    dx = 1 / 64
+    margin = np.sqrt(17.0 * dx * dx) * 1.01 + 2 * dx
+    P = _dziuk_surface_points(80, 2)
+    nrm = _dziuk_normal(P)
+    t = np.random.default_rng(3).uniform(-1.0, 1.0, len(P)) * 2 * margin
+    assert _candidate_filter(dziuk(), P + t[:, None] * nrm, margin).all()

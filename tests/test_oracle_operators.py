@@ -152,3 +152,41 @@ def test_table31_digits():
         got = _table31_error(dx)
         tol = 0.01 if dx > 0.06 else 0.005
         assert abs(got - want) <= tol * want + 0.5e-2 * 10 ** np.floor(np.log10(want)), (dx, got, want)
+
+
+def test_vardiff_operator_definition_and_unit_coefficient():
+    """L~ = sum D^b diag(A^f a) D^f (Sec. 4.5.6) written row by row for a few
+    nodes; with a = 1 the variable-diffusion M is the paper-form M (Eq. 3.3)."""
+    from oracle.operators import VarDiffOperators, lap_vardiff
+    band = build_band(sphere(), 1 / 8)
+    rng = np.random.default_rng(3)
+    a = rng.uniform(1.0, 2.5, band.nb)
+    Lt = lap_vardiff(band, a).tocsr()
+    h2 = band.dx ** 2
+    nbk = band.neighbour_keys(band.keys)
+    for i in rng.integers(0, band.nb, 20):
+        row = np.zeros(band.nb)
+        for k in band.index_in_band(nbk[i]):
+            if k >= 0:
+                row[k] += 0.5 * (a[i] + a[k]) / h2
+                row[i] -= 0.5 * (a[i] + a[k]) / h2
+        assert np.abs(Lt[i].toarray().ravel() - row).max() <= 1e-12 * np.abs(row).max()
+    ones = VarDiffOperators(band, np.ones(band.nb))
+    assert np.abs((ones.M - paper_M(band)).toarray()).max() <= 1e-10 * gamma(band)
+
+
+def test_vardiff_sphere_closed_form_second_order():
+    """Sec. 4.5.6 on the unit sphere: u = cos(phi), a = cos(phi) + 1.5,
+    f = 2 cos(phi)(cos(phi) + 1.5) - sin(phi)^2 + u; the direct solution
+    converges to u at second order."""
+    import scipy.sparse.linalg as spla
+    from oracle.operators import VarDiffOperators
+    errs = []
+    for dx in [1 / 8, 1 / 16]:
+        band = build_band(sphere(), dx)
+        u, a, f = synth.sphere_vardiff(band.cp[: band.nb])
+        op = VarDiffOperators(band, a)
+        uh = spla.spsolve(op.A_matrix(1.0).tocsc(), f)
+        errs.append(np.abs(uh - u).max() / np.abs(u).max())
+    order = np.log2(errs[0] / errs[1])
+    assert 1.8 < order < 2.3, (errs, order)

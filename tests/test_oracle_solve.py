@@ -146,3 +146,20 @@ def test_variable_c_restricted_to_coarse_levels():
     assert rep.converged and rep.iters <= 20
     ud = spla.spsolve(fine.ops.A_matrix(fine.c).tocsc(), f)
     assert np.abs(u - ud).max() <= 1e-10 * np.abs(ud).max()
+
+
+def test_vardiff_vcycle_solution_equals_direct_solve():
+    """Variable diffusion (Sec. 4.5.6) through the V-cycle: the coefficient a is
+    restricted to the coarse levels like c, the defect correction converges at a
+    level-independent-ish rate and its solution is the direct one."""
+    a_fn = lambda y: synth.sphere_vardiff(y)[1]
+    H = build_hierarchy(sphere(), 1 / 16, 1 / 8,
+                        opts=MGOptions(smoother="jacobi", nu1=3, nu2=3, omega=0.8,
+                                       residual="plain", operator="vardiff"), a_fn=a_fn)
+    fine, coarse = H.levels
+    assert np.array_equal(coarse.ops.a, fine.R @ fine.ops.a)
+    _, _, f = synth.sphere_vardiff(fine.band.cp[: fine.band.nb])
+    u, rep = solve(H, f, tol=1e-12, max_iter=40)
+    assert rep.converged and rep.iters <= 20, rep.iters
+    ud = spla.spsolve(fine.ops.A_matrix(1.0).tocsc(), f)
+    assert np.abs(u - ud).max() <= 1e-10 * np.abs(ud).max()
