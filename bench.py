@@ -641,7 +641,7 @@ def main():
     ap.add_argument("--inner", type=int, default=3, help="FP32 V-cycles per outer iteration")
     ap.add_argument("--residual", default="plain", choices=["extended", "plain"],
                     help="residual restricted in the V-cycle: f - A(E u) (Sec. 4.4) or f - A u")
-    ap.add_argument("--nu", type=int, default=3, help="pre- and post-smoothing sweeps")
+    ap.add_argument("--nu", type=int, default=4, help="pre- and post-smoothing sweeps")
     ap.add_argument("--no-learned", action="store_true", help="skip the learned-smoother form")
     ap.add_argument("--workload", default="sphere256", choices=sorted(WORKLOADS))
     ap.add_argument("--only-mixed", action="store_true",

@@ -200,6 +200,16 @@ typedef struct cpm_mg_opts {
   const double* a_device;   /* CPM_OP_VARDIFF: the diffusion coefficient a(cp(x))
                                > 0 on the finest band (device, length n_band);
                                coarse levels take its restriction, like c      */
+  int32_t relative;         /* CPM_OP_MBR, Jacobi: 1 = the V-cycles evaluate
+                               their residuals and Jacobi updates in the
+                               relative form of cpm_residual (extension of
+                               u - u_ref per tile, differences formed from
+                               exact inputs), which lowers the FP32 rounding
+                               floor of the FP32 V-cycle; 0 = the direct form  */
+  int32_t ext_variant;      /* FP32 extension work decomposition of every level
+                               (see cpm_hier_ext_tuning): 0 = chosen per level
+                               by timing when the hierarchy is built; 1, 2, 3 =
+                               variant 0, 1, 2 everywhere                       */
 } cpm_mg_opts;
 
 typedef enum cpm_op_form { CPM_OP_MBR = 0, CPM_OP_PAPER = 1, CPM_OP_VARDIFF = 2 } cpm_op_form;
@@ -219,6 +229,17 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts,
 
 /* Number of levels and |B| of level l (host outputs, synchronous). */
 cpm_status cpm_hier_info(cpm_hier h, int32_t* n_levels, int32_t level, int64_t* n_band);
+
+/*
+ * The work decomposition of level `level`'s FP32 extension, chosen when the
+ * hierarchy was built by timing each candidate on that level (three launches
+ * over B+ after a warm-up): 0 one CTA per extension tile and one thread per
+ * point, 1 persistent CTAs that stage the next tile while evaluating the
+ * current one, 2 one thread per chunk of points that share a stencil base.
+ * variant: host int32 (may be NULL); ms: host array of 3 doubles, the measured
+ * milliseconds of each candidate (may be NULL).  No counterpart in the paper.
+ */
+cpm_status cpm_hier_ext_tuning(cpm_hier h, int32_t level, int32_t* variant, double* ms);
 
 /*
  * Mu = M u on level `level` (0 = finest).  CPM_OP_MBR: w = E u on B+, then

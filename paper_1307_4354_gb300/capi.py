@@ -39,7 +39,7 @@ class cpm_mg_opts(C.Structure):
                 ("c", C.c_double), ("c_device", C.c_void_p), ("residual_mode", C.c_int32),
                 ("coarse_sweeps", C.c_int32), ("coarse_f64_max", C.c_int32),
                 ("coarse_dense_max", C.c_int32), ("op_form", C.c_int32), ("cycle", C.c_int32),
-                ("a_device", C.c_void_p)]
+                ("a_device", C.c_void_p), ("relative", C.c_int32), ("ext_variant", C.c_int32)]
 
 
 class cpm_solve_opts(C.Structure):
@@ -95,6 +95,7 @@ _PROTOS = {
     "cpm_build_hierarchy": (C.c_int, [C.c_void_p, C.POINTER(cpm_mg_opts), C.c_void_p,
                                       C.POINTER(C.c_void_p)]),
     "cpm_hier_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_int64)]),
+    "cpm_hier_ext_tuning": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(C.c_int32), C.POINTER(C.c_double)]),
     "cpm_apply": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p]),
     "cpm_extend": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
                              C.c_void_p]),
@@ -209,6 +210,13 @@ def cpm_hier_info(h: int, level: int = 0):
     nl, nb = C.c_int32(), C.c_int64()
     _check(lib().cpm_hier_info(C.c_void_p(h), C.byref(nl), level, C.byref(nb)), "cpm_hier_info")
     return nl.value, nb.value
+
+
+def cpm_hier_ext_tuning(h: int, level: int):
+    v = C.c_int32()
+    ms = (C.c_double * 3)()
+    _check(lib().cpm_hier_ext_tuning(C.c_void_p(h), level, C.byref(v), ms), "cpm_hier_ext_tuning")
+    return v.value, list(ms)
 
 
 def cpm_apply(h: int, level: int, prec: int, u_ptr: int, Mu_ptr: int, stream: int = 0):

@@ -180,6 +180,8 @@ struct Level {
   // chunks: runs of at most kChunkMax consecutive E-order points of one tile
   // that share one stencil base (and are all in B or all in G); one thread
   // loads the base's 4^d values once and evaluates every point of the chunk
+  int ext_variant = 0;        // FP32 extension variant chosen by timing (ExtVariant)
+  float ext_ms[3] = {0.f, 0.f, 0.f};
   int32_t nchunks = 0;
   DBuf<uint32_t> echunk;      // first E-order point | (count - 1) << 26
   DBuf<int32_t> tile_cstart;  // ntiles + 1 offsets into echunk

@@ -13,6 +13,8 @@
 // shared memory.  Records are stored in this "E order" (band index and base
 // position inside the brick in one 32-bit word, fractions SoA); results are
 // written back to the band index.
+#include <algorithm>
+
 #include "ops.cuh"
 
 namespace cpm {
@@ -164,7 +166,7 @@ __global__ void k_tile_sort(const int32_t* tile_start, int64_t nplus, int32_t nB
 // kChunkMax points.  One thread per tile counts (emit = false) or writes
 // (emit = true) its chunks.
 #ifndef CPM_EXT_CHUNK
-#define CPM_EXT_CHUNK 4
+#define CPM_EXT_CHUNK 2
 #endif
 constexpr int kChunkMax = CPM_EXT_CHUNK;
 static_assert(kChunkMax >= 1 && kChunkMax <= 8, "chunk count must fit in 3 bits");
@@ -574,12 +576,123 @@ __device__ __forceinline__ float contract_regs(const float4 (&v)[DIM == 3 ? 16 :
 
 // FP32 extension by chunks (1) or one thread per point (0, the default:
 // measured faster on GB300 at dx = 1/256: 110 us against 198-294 us).
+// FP32 extension, persistent and software-pipelined: a fixed grid of CTAs, each
+// looping over tiles blockIdx.x, blockIdx.x + gridDim.x, ...; while it
+// evaluates the points of one tile from one shared-memory box it has the row
+// loads of its next tile in flight (into registers, one box row per thread)
+// and writes them into the other box afterwards, so the staging latency of a
+// tile hides behind the arithmetic of the previous one.
+#ifndef CPM_EXT_PIPELINED
+#define CPM_EXT_PIPELINED 0
+#endif
+constexpr bool kPipelined = CPM_EXT_PIPELINED != 0;
+constexpr int kPipeThreads = 64;
+
+template <int DIM>
+__global__ void __launch_bounds__(kPipeThreads) k_extend_pipe(LevelView<float> L,
+                                                              const float* __restrict__ u,
+                                                              float* __restrict__ w, bool with_ghost) {
+  constexpr int RS = kRS;
+  constexpr int NZ = DIM == 3 ? 7 : 1;
+  constexpr int NB = DIM == 3 ? 8 : 4;
+  __shared__ __align__(16) float win[2][NZ * 7 * RS];
+  __shared__ uint32_t smask[2][NB][2];
+  __shared__ int32_t sstart[2][NB][2];
+  static_assert(kPipeThreads >= 49, "one box row per thread");
+  int32_t tile = blockIdx.x;
+  if (tile >= L.ntiles) return;
+  // the rows of tile t: addresses from its masks in buffer b, values into v
+  auto load_rows = [&](int32_t t, int b, float v[7], int& ylo_o, int& z_o, int& y_o, int& xlo_o,
+                       int& xhi_o) -> bool {
+    const uint32_t tbox = __ldg(L.tile_box + t);
+    const int xlo = tbox & 3, xhi = (tbox >> 2) & 3;
+    const int ylo = (tbox >> 4) & 3, yhi = (tbox >> 6) & 3;
+    const int zlo = DIM == 3 ? (tbox >> 8) & 3 : 0, zhi = DIM == 3 ? ((tbox >> 10) & 3) + 3 : 0;
+    const int ny = yhi + 4 - ylo;
+    const int r = threadIdx.x;
+    if (r >= ny * (zhi + 1 - zlo)) return false;
+    const int y = ylo + r % ny, z = zlo + r / ny;
+    const int jyz = ((y >> 2) << 1) | ((z >> 2) << 2);
+    const int half = (z >> 1) & 1;
+    const int shift = ((y & 3) << 2) | ((z & 1) << 4);
+    const uint32_t wa = smask[b][jyz][half], wb = smask[b][jyz | 1][half];
+    const uint32_t rba = (wa >> shift) & 0xFu, rbb = (wb >> shift) & 0xFu;
+    const uint32_t below = (1u << shift) - 1u;
+    int32_t ca = sstart[b][jyz][half] + __popc(wa & below) + __popc(rba & ((1u << xlo) - 1u));
+    int32_t cb = sstart[b][jyz | 1][half] + __popc(wb & below);
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      const int x = xlo + i;
+      v[i] = 0.f;
+      if (x <= xhi + 3) {
+        const bool hi = x >= 4;
+        if (((hi ? rbb : rba) >> (x & 3)) & 1u) v[i] = __ldg(u + (hi ? cb++ : ca++));
+      }
+    }
+    y_o = y;
+    z_o = z;
+    ylo_o = ylo;
+    xlo_o = xlo;
+    xhi_o = xhi;
+    return true;
+  };
+  auto load_masks = [&](int32_t t, int b) {
+    if (threadIdx.x < NB) {
+      const int j = threadIdx.x;
+      const uint64_t m = __ldg(L.tile_mask + 8 * (int64_t)t + j);
+      const int32_t s0 = __ldg(L.tile_bstart + 8 * (int64_t)t + j);
+      smask[b][j][0] = (uint32_t)m;
+      smask[b][j][1] = (uint32_t)(m >> 32);
+      sstart[b][j][0] = s0;
+      sstart[b][j][1] = s0 + __popc((uint32_t)m);
+    }
+  };
+  auto store_rows = [&](int b, const float v[7], int y, int z, int xlo, int xhi) {
+    float* row = win[b] + (z * 7 + y) * RS;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (xlo + i <= xhi) store4(row + 4 * (xlo + i), v[i], v[i + 1], v[i + 2], v[i + 3]);
+  };
+  // prologue: the first tile's box
+  int buf = 0;
+  load_masks(tile, 0);
+  __syncthreads();
+  {
+    float v[7];
+    int ylo, y, z, xlo, xhi;
+    if (load_rows(tile, 0, v, ylo, z, y, xlo, xhi)) store_rows(0, v, y, z, xlo, xhi);
+  }
+  __syncthreads();
+  for (; tile < L.ntiles; tile += gridDim.x) {
+    const int32_t next = tile + gridDim.x;
+    const bool has_next = next < L.ntiles;
+    if (has_next) load_masks(next, buf ^ 1);
+    __syncthreads();
+    float v[7];
+    int ylo = 0, y = 0, z = 0, xlo = 0, xhi = 0;
+    const bool row = has_next && load_rows(next, buf ^ 1, v, ylo, z, y, xlo, xhi);
+    // the points of this tile from win[buf]
+    const int32_t beg = __ldg(L.tile_start + tile);
+    const int32_t end = with_ghost ? __ldg(L.tile_start + tile + 1) : __ldg(L.tile_mid + tile);
+    for (int32_t k = beg + threadIdx.x; k < end; k += kPipeThreads) {
+      const uint32_t rec = __ldg(L.erec + k);
+      PointWeights<float, DIM> pw;
+      pw.load(L, k);
+      const float* base = win[buf] + ((rec >> 4) & 3) * 7 * RS + ((rec >> 2) & 3) * RS + (rec & 3) * 4;
+      w[rec >> 6] = contract<DIM>(base, pw);
+    }
+    if (row) store_rows(buf ^ 1, v, y, z, xlo, xhi);
+    __syncthreads();
+    buf ^= 1;
+  }
+}
+
 #ifndef CPM_EXT_CHUNKED
 #define CPM_EXT_CHUNKED 0
 #endif
 constexpr bool kChunked = CPM_EXT_CHUNKED != 0;
 #ifndef CPM_EXT_CHUNK_THREADS
-#define CPM_EXT_CHUNK_THREADS 64
+#define CPM_EXT_CHUNK_THREADS 32
 #endif
 constexpr int kChunkThreads = CPM_EXT_CHUNK_THREADS;
 constexpr int kStageMax = 256;  // points of a tile whose records are staged in shared memory
@@ -643,36 +756,87 @@ __global__ void __launch_bounds__(kChunkThreads) k_extend_chunks(LevelView<float
   }
 }
 
+// The FP32 extension's work decomposition ("tile variant") of a level:
+// EXT_TILES one CTA per tile, one thread per point; EXT_PIPE persistent CTAs
+// with the next tile's staging in flight; EXT_CHUNKS one thread per chunk of
+// points with one stencil base.  The hierarchy picks one per level by timing
+// (tune_extension).  CPM_EXT_PIPELINED / CPM_EXT_CHUNKED force a variant.
+template <typename T>
+static void extend_variant(const LevelView<T>& L, int variant, const T* u, T* w, bool with_ghost,
+                           cudaStream_t st) {
+  const int32_t nt = L.ntiles;
+  if constexpr (sizeof(T) == 4) {
+    if (variant == EXT_PIPE) {
+      const unsigned grid = (unsigned)std::min<int32_t>(nt, 152 * 16);
+      if (L.dim == 3)
+        k_extend_pipe<3><<<grid, kPipeThreads, 0, st>>>(L, u, w, with_ghost);
+      else
+        k_extend_pipe<2><<<grid, kPipeThreads, 0, st>>>(L, u, w, with_ghost);
+      return;
+    }
+    if (variant == EXT_CHUNKS) {
+      if (L.dim == 3)
+        k_extend_chunks<3><<<nt, kChunkThreads, 0, st>>>(L, u, w, with_ghost);
+      else
+        k_extend_chunks<2><<<nt, kChunkThreads, 0, st>>>(L, u, w, with_ghost);
+      return;
+    }
+  }
+  if (L.dim == 3)
+    k_extend_tiles<T, 3><<<nt, kExtThreads, 0, st>>>(L, u, w, with_ghost, nullptr);
+  else
+    k_extend_tiles<T, 2><<<nt, kExtThreads, 0, st>>>(L, u, w, with_ghost, nullptr);
+}
+
 template <typename T>
 void launch_extend(const LevelView<T>& L, const T* u, T* w, int32_t npts, cudaStream_t st) {
   if (npts <= 0) return;
-  const int32_t nt = L.ntiles;
-  if (nt <= 0) return;
-  const bool with_ghost = npts > L.nB;
-  if constexpr (sizeof(T) == 4 && kChunked) {
-    if (L.dim == 3)
-      k_extend_chunks<3><<<nt, kChunkThreads, 0, st>>>(L, u, w, with_ghost);
-    else
-      k_extend_chunks<2><<<nt, kChunkThreads, 0, st>>>(L, u, w, with_ghost);
-  } else {
-    if (L.dim == 3)
-      k_extend_tiles<T, 3><<<nt, kExtThreads, 0, st>>>(L, u, w, with_ghost, nullptr);
-    else
-      k_extend_tiles<T, 2><<<nt, kExtThreads, 0, st>>>(L, u, w, with_ghost, nullptr);
-  }
+  if (L.ntiles <= 0) return;
+  int variant = L.ext_variant;
+  if (kPipelined) variant = EXT_PIPE;
+  if (kChunked) variant = EXT_CHUNKS;
+  extend_variant<T>(L, variant, u, w, npts > L.nB, st);
   count_launch();
 }
 
-void launch_extend_rel(const LevelView<double>& L, const double* u, double* delta, double* refv,
-                       cudaStream_t st) {
+int tune_extension(const LevelView<float>& L, const float* u, float* w, cudaStream_t st, float ms[3]) {
+  int best = EXT_TILES;
+  for (int v = 0; v < 3; ++v) ms[v] = 0.f;
+  if (L.ntiles <= 0) return best;
+  cudaEvent_t e0, e1;
+  CPM_CUDA_TRY(cudaEventCreate(&e0));
+  CPM_CUDA_TRY(cudaEventCreate(&e1));
+  constexpr int kReps = 3;
+  for (int v = 0; v < 3; ++v) {
+    extend_variant<float>(L, v, u, w, true, st);  // warm-up
+    CPM_CUDA_TRY(cudaEventRecord(e0, st));
+    for (int r = 0; r < kReps; ++r) extend_variant<float>(L, v, u, w, true, st);
+    CPM_CUDA_TRY(cudaEventRecord(e1, st));
+    CPM_CUDA_TRY(cudaEventSynchronize(e1));
+    CPM_CUDA_TRY(cudaEventElapsedTime(&ms[v], e0, e1));
+    ms[v] /= kReps;
+    if (ms[v] < ms[best]) best = v;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  CPM_CUDA_TRY(cudaGetLastError());
+  return best;
+}
+
+template <typename T>
+void launch_extend_rel(const LevelView<T>& L, const T* u, T* delta, T* refv, cudaStream_t st) {
   const int32_t nt = L.ntiles;
   if (nt <= 0) return;
   if (L.dim == 3)
-    k_extend_tiles<double, 3, true><<<nt, kExtThreads, 0, st>>>(L, u, delta, true, refv);
+    k_extend_tiles<T, 3, true><<<nt, kExtThreads, 0, st>>>(L, u, delta, true, refv);
   else
-    k_extend_tiles<double, 2, true><<<nt, kExtThreads, 0, st>>>(L, u, delta, true, refv);
+    k_extend_tiles<T, 2, true><<<nt, kExtThreads, 0, st>>>(L, u, delta, true, refv);
   count_launch();
 }
+template void launch_extend_rel<double>(const LevelView<double>&, const double*, double*, double*,
+                                        cudaStream_t);
+template void launch_extend_rel<float>(const LevelView<float>&, const float*, float*, float*,
+                                       cudaStream_t);
 
 template void launch_extend<double>(const LevelView<double>&, const double*, double*, int32_t,
                                     cudaStream_t);

@@ -88,8 +88,9 @@ struct Transfer {
 
 template <typename T>
 struct Work {
-  DBuf<T> u, f, r, w, tmp, v;
-  void alloc(int64_t nB, int64_t nplus, bool paper) {
+  DBuf<T> u, f, r, w, tmp, v, refv;
+  void alloc(int64_t nB, int64_t nplus, bool paper, bool relative) {
+    if (relative) refv.alloc(nplus);  // reference values of the relative extension
     u.alloc(nB);
     f.alloc(nB);
     r.alloc(nB);
@@ -140,6 +141,7 @@ LevelView<double> HLevel::view<double>() const {
   v.efr = lev->efr32.get();
   v.ew64 = lev->ew64.get();
   v.ntiles = lev->ntiles;
+  v.ext_variant = lev->ext_variant;
   v.echunk = lev->echunk.get();
   v.tile_cstart = lev->tile_cstart.get();
   v.tile_cmid = lev->tile_cmid.get();
@@ -167,6 +169,7 @@ LevelView<float> HLevel::view<float>() const {
   v.efr = lev->efr32.get();
   v.ew64 = lev->ew64.get();
   v.ntiles = lev->ntiles;
+  v.ext_variant = lev->ext_variant;
   v.echunk = lev->echunk.get();
   v.tile_cstart = lev->tile_cstart.get();
   v.tile_cmid = lev->tile_cmid.get();
@@ -254,8 +257,8 @@ static void alloc_workspace(const cpm_hier_s& H, Workspace& W, double* norms_slo
   for (size_t l = 0; l < H.L.size(); ++l) {
     const int64_t nB = H.L[l].lev->nB, np = H.L[l].lev->nplus();
     const bool paper = H.opts.op_form != CPM_OP_MBR;
-    W.w64[l].alloc(nB, np, paper);
-    W.w32[l].alloc(nB, np, paper);
+    W.w64[l].alloc(nB, np, paper, H.opts.relative != 0);
+    W.w32[l].alloc(nB, np, paper, H.opts.relative != 0);
   }
   const int64_t nB0 = H.L[0].lev->nB;
   W.part_blocks = std::max<int>(std::max(lap_blocks_f64(H.L[0].view<double>()),
@@ -304,6 +307,10 @@ static void level_op(cpm_hier_s* H, Workspace& W, int l, LapMode mode, const T* 
     launch_extend<T>(v, u, w.w.get(), v.nB, st);
     launch_paper<T>(v, mode, u, w.v.get(), w.w.get(), f, lv.cvec<T>(), (T)H->c, dA, out, u_inout,
                     part, a, st);
+  } else if (H->opts.relative && (mode == LAP_RESID || mode == LAP_JACOBI)) {
+    launch_extend_rel<T>(v, u, w.w.get(), w.refv.get(), st);
+    launch_lap_rel<T>(v, mode == LAP_RESID ? LAP_RESID_REL : LAP_JAC_REL, u, w.w.get(), w.refv.get(), f,
+                      lv.cvec<T>(), (T)H->c, dA, out, u_inout, part, st);
   } else {
     launch_extend<T>(v, u, w.w.get(), (int32_t)v.nplus, st);
     launch_lap<T>(v, mode, u, w.w.get(), f, lv.cvec<T>(), (T)H->c, dA, (T)H->opts.omega, out,
@@ -718,6 +725,9 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
             CPM_ERR_ARG, "unknown op_form");
   CPM_CHECK((o.op_form == CPM_OP_VARDIFF) == (o.a_device != nullptr), CPM_ERR_ARG,
             "a_device is given exactly with op_form CPM_OP_VARDIFF");
+  CPM_CHECK(o.relative == 0 || (o.relative == 1 && o.op_form == CPM_OP_MBR), CPM_ERR_ARG,
+            "relative = 1 is for the CPM_OP_MBR operator");
+  CPM_CHECK(o.ext_variant >= 0 && o.ext_variant <= 3, CPM_ERR_ARG, "ext_variant must be 0 .. 3");
   CPM_CHECK(o.op_form == CPM_OP_MBR || o.smoother != CPM_SMOOTH_RM, CPM_ERR_ARG,
             "the paper-form operator is smoothed on A (Jacobi or red-black Gauss-Seidel)");
   if (!(o.c > 0)) o.c = 1.0;
@@ -883,7 +893,30 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
 
   // solve buffers
   alloc_workspace(*H, H->ws);
+  // the FP32 extension variant of every level, by timing (its "tile": one
+  // thread per point, persistent pipelined tiles, or chunks of one base)
+  for (int l = 0; l < nl; ++l) {
+    Level& lev = *H->L[l].lev;
+    if (o.ext_variant > 0) {
+      lev.ext_variant = o.ext_variant - 1;
+      continue;
+    }
+    CPM_CUDA_TRY(cudaMemsetAsync(H->ws.w32[l].u.get(), 0, sizeof(float) * lev.nB, st));
+    lev.ext_variant = tune_extension(H->L[l].view<float>(), H->ws.w32[l].u.get(), H->ws.w32[l].w.get(),
+                                     st, lev.ext_ms);
+  }
   *out = H.release();
+  CPM_API_END
+}
+
+cpm_status cpm_hier_ext_tuning(cpm_hier h, int32_t level, int32_t* variant, double* ms) {
+  CPM_API_BEGIN
+  CPM_CHECK(h != nullptr, CPM_ERR_ARG, "hierarchy is NULL");
+  CPM_CHECK(level >= 0 && level < (int)h->L.size(), CPM_ERR_ARG, "level out of range");
+  const Level& lev = *h->L[level].lev;
+  if (variant) *variant = lev.ext_variant;
+  if (ms)
+    for (int v = 0; v < 3; ++v) ms[v] = lev.ext_ms[v];
   CPM_API_END
 }
 

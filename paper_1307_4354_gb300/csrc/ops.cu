@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(256) k_lap(LevelView<T> L, const T* u, const T
       }
       const T wi = w[i];
       T s = T(0), Mu;
-      if (MODE == LAP_RESID_REL) {
+      if (MODE == LAP_RESID_REL || MODE == LAP_JAC_REL) {
         const T ri = refv[i];
 #pragma unroll
         for (int q = 0; q < 2 * DIM; ++q) {
@@ -269,7 +269,7 @@ __global__ void __launch_bounds__(256) k_lap_idx(LevelView<T> L, const T* u, con
     } else {
       const T wi = w[i];
       T s = T(0), Mu;
-      if (MODE == LAP_RESID_REL) {
+      if (MODE == LAP_RESID_REL || MODE == LAP_JAC_REL) {
         const T ri = refv[i];
 #pragma unroll
         for (int q = 0; q < 2 * DIM; ++q) s += (refv[k[q]] - ri) + (w[k[q]] - wi);
@@ -331,6 +331,16 @@ void launch_lap(const LevelView<T>& L, LapMode mode, const T* u, const T* w, con
   if (mode == LAP_JACOBI) lap_dim<LAP_JACOBI>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, (const T*)nullptr, st);
   if (mode == LAP_JAC_RED) lap_dim<LAP_JAC_RED>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, (const T*)nullptr, st);
   if (mode == LAP_JAC_BLACK) lap_dim<LAP_JAC_BLACK>(L, u, w, f, cvec, cval, dA, omega, out, u_inout, part, (const T*)nullptr, st);
+}
+
+template <typename T>
+void launch_lap_rel(const LevelView<T>& L, LapMode mode, const T* u, const T* delta, const T* refv,
+                    const T* f, const T* cvec, T cval, const T* dA, T* out, T* u_inout, double* part,
+                    cudaStream_t st) {
+  if (mode == LAP_RESID_REL)
+    lap_dim<LAP_RESID_REL>(L, u, delta, f, cvec, cval, dA, T(0), out, u_inout, part, refv, st);
+  else
+    lap_dim<LAP_JAC_REL>(L, u, delta, f, cvec, cval, dA, T(0), out, u_inout, part, refv, st);
 }
 
 void launch_resid_rel(const LevelView<double>& L, const double* u, const double* delta,
@@ -955,6 +965,8 @@ void invert_dense(double* A, int32_t n, cudaStream_t st, int32_t* err) {
                                    cudaStream_t);                                                \
   template void launch_transfer<T>(const TransferView<T>&, const T*, T*, bool, cudaStream_t);    \
   template void launch_lap_band<T>(const LevelView<T>&, const T*, T*, cudaStream_t);            \
+  template void launch_lap_rel<T>(const LevelView<T>&, LapMode, const T*, const T*, const T*,   \
+                                  const T*, const T*, T, const T*, T*, T*, double*, cudaStream_t); \
   template void launch_paper<T>(const LevelView<T>&, LapMode, const T*, const T*, const T*,     \
                                 const T*, const T*, T, const T*, T*, T*, double*, const T*,      \
                                 cudaStream_t);                                                   \

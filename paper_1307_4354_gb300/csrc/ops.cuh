@@ -28,6 +28,7 @@ struct LevelView {
   const float* efr;     // E-order FP32 fractions
   const double* ew64;   // E-order FP64 weights
   int32_t ntiles;
+  int ext_variant;            // FP32 extension work decomposition (ExtVariant)
   const uint32_t* echunk;     // chunk records (ext.cu)
   const int32_t* tile_cstart; // ntiles + 1 chunk offsets
   const int32_t* tile_cmid;   // per tile: end of its chunks of B
@@ -50,20 +51,32 @@ struct TransferView {
 };
 
 enum LapMode { LAP_APPLY = 0, LAP_RESID = 1, LAP_JACOBI = 2, LAP_RESID_REL = 3,
-               LAP_JAC_RED = 4, LAP_JAC_BLACK = 5 };  // Jacobi update of one colour only
+               LAP_JAC_RED = 4, LAP_JAC_BLACK = 5,  // Jacobi update of one colour only
+               LAP_JAC_REL = 6 };                    // Jacobi update from the relative extension
 // Red (0) / black (1): parity of the sum of the grid coordinates.  Bricks start
 // at multiples of 4, so the parity of the local coordinates inside a brick is
 // that of the global ones.
 __host__ __device__ inline int node_colour_local(int l) { return ((l & 3) + ((l >> 2) & 3) + (l >> 4)) & 1; }
 
+enum ExtVariant { EXT_TILES = 0, EXT_PIPE = 1, EXT_CHUNKS = 2 };
+// Time the three FP32 extension variants on a level (over B+, one warm-up and
+// three timed launches each, CUDA events on st) and return the fastest; ms[v]
+// gets each variant's time.  u, w: device scratch of nB and nB + nG floats.
+int tune_extension(const LevelView<float>& L, const float* u, float* w, cudaStream_t st, float ms[3]);
+
 // w = E u on the first npts points of B+ (npts = nB or nB + nG).
 template <typename T>
 void launch_extend(const LevelView<T>& L, const T* u, T* w, int32_t npts, cudaStream_t st);
 
-// FP64 extension over B+ in relative form: delta_j = (E u)_j - ref_j with
+// Extension over B+ in relative form: delta_j = (E u)_j - ref_j with
 // ref_j = u at a reference node of j's tile (see k_extend_tiles).
-void launch_extend_rel(const LevelView<double>& L, const double* u, double* delta, double* refv,
-                       cudaStream_t st);
+template <typename T>
+void launch_extend_rel(const LevelView<T>& L, const T* u, T* delta, T* refv, cudaStream_t st);
+// RESID_REL / JAC_REL passes from delta and refv (launch_lap with refv).
+template <typename T>
+void launch_lap_rel(const LevelView<T>& L, LapMode mode, const T* u, const T* delta, const T* refv,
+                    const T* f, const T* cvec, T cval, const T* dA, T* out, T* u_inout, double* part,
+                    cudaStream_t st);
 // FP64 residual r = f - c u + M u from the relative extension: every
 // difference w_k - w_i = (ref_k - ref_i) + (delta_k - delta_i) and
 // w_i - u_i = (ref_i - u_i) + delta_i is formed from exact inputs, so the

@@ -88,7 +88,8 @@ class Hierarchy:
                  c_device: torch.Tensor | None = None, residual: str = "extended",
                  coarse_sweeps: int = 0, coarse_f64_max: int = 0, coarse_dense_max: int = 0,
                  op_form: str = "mbr", transfer_deg: int = 1, cycle: int = 1,
-                 a_device: torch.Tensor | None = None, stream=None):
+                 a_device: torch.Tensor | None = None, relative: bool = False,
+                 ext_variant: int | None = None, stream=None):
         o = capi.cpm_mg_opts()
         o.coarsest_dx, o.nu1, o.nu2, o.omega = coarsest_dx, nu1, nu2, omega
         o.smoother, o.transfer_deg, o.c = _SMOOTHERS[smoother], transfer_deg, c
@@ -99,10 +100,16 @@ class Hierarchy:
         o.op_form = {"mbr": capi.CPM_OP_MBR, "paper": capi.CPM_OP_PAPER,
                      "vardiff": capi.CPM_OP_VARDIFF}[op_form]
         o.a_device = _ptr(a_device, torch.float64, band.nb) if a_device is not None else None
+        o.relative = int(relative)
+        o.ext_variant = 0 if ext_variant is None else int(ext_variant) + 1
         o.c_device = _ptr(c_device, torch.float64, band.nb) if c_device is not None else None
         self.band = band
         self.handle = capi.cpm_build_hierarchy(band.handle, o, _stream(stream))
         self.n_levels, self.nb = capi.cpm_hier_info(self.handle, 0)
+
+    def ext_tuning(self, level: int = 0):
+        """(FP32 extension variant chosen for the level, ms of each candidate)."""
+        return capi.cpm_hier_ext_tuning(self.handle, level)
 
     def level_size(self, level: int) -> int:
         return capi.cpm_hier_info(self.handle, level)[1]

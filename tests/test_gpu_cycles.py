@@ -74,3 +74,33 @@ def test_full_multigrid_first_iteration(kind, params, dx):
     for mode in ("f64", "mixed"):
         u, rep = H.solve(ft, tol=1e-10, max_iter=60, mode=mode, fmg=True)
         assert rep["converged"], (mode, rep)
+
+
+@pytest.mark.parametrize("kind,params,dx", [("circle", (), 1 / 64), ("sphere", (), 1 / 32)])
+def test_relative_form_vcycle_parity(kind, params, dx):
+    """relative = 1: the V-cycle's residuals and Jacobi updates in the relative
+    form (the same operator, other rounding) equal the oracle's cycle in FP64,
+    and the FP32 cycles of both forms stay within single precision of it on
+    smooth data."""
+    torch, pkg = require_cuda()
+    g = pkg.Band(kind, params, dx)
+    H = pkg.Hierarchy(g, coarsest_dx=1 / 8, nu1=3, nu2=3, omega=0.8, residual="plain", relative=True)
+    H0 = pkg.Hierarchy(g, coarsest_dx=1 / 8, nu1=3, nu2=3, omega=0.8, residual="plain")
+    OH = build_hierarchy(oracle_surface(kind, params), dx, 1 / 8,
+                         opts=MGOptions(smoother="jacobi", nu1=3, nu2=3, omega=0.8, residual="plain"))
+    perm = perm_gpu_to_oracle(g, OH.fine.band)
+    nb = OH.fine.band.nb
+    f_o = synth.random_band_vector(nb, 53)
+    ref = vcycle(OH, np.zeros(nb), f_o)[perm]
+    u = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    H.vcycle(torch.from_numpy(f_o[perm]).cuda(), u)
+    assert np.abs(u.cpu().numpy() - ref).max() <= 1e-10 * np.abs(ref).max()
+    fn = synth.circle_fourier if kind == "circle" else synth.sphere_harmonics
+    _, fs = fn(OH.fine.band.cp[:nb])
+    ref = vcycle(OH, np.zeros(nb), fs)[perm]
+    errs = []
+    for h in (H, H0):
+        u32 = torch.zeros(nb, dtype=torch.float32, device="cuda")
+        h.vcycle(torch.from_numpy(fs[perm]).float().cuda(), u32)
+        errs.append(np.abs(u32.double().cpu().numpy() - ref).max() / np.abs(ref).max())
+    assert errs[0] <= 1e-4 and errs[1] <= 1e-4, errs

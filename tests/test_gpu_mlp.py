@@ -122,9 +122,12 @@ def test_save_and_load_round_trip(tmp_path):
     d2 = H.smoother_correction(r32)
     assert torch.equal(d1, d2)
     # training continues from the saved Adam state: the same next step on both
+    # (to rounding: the transposed extension of the gradient sums with atomics)
+    p0 = sm.get_params()
     sm.train([(H, fields[0])], steps=1)
     back.train([(H, fields[0])], steps=1)
-    assert np.array_equal(back.get_params(), sm.get_params())
+    p1, p2 = sm.get_params(), back.get_params()
+    assert np.abs(p1 - p2).max() <= 1e-3 * np.abs(p1 - p0).max()
     bad = tmp_path / "bad.bin"
     bad.write_bytes(b"not a network")
     with pytest.raises(pkg.capi.CpmError):
@@ -132,22 +135,24 @@ def test_save_and_load_round_trip(tmp_path):
 
 
 def test_trained_network_gains_over_jacobi_on_a_held_out_surface():
-    """The network trained on residuals of seeded ellipsoids and tori (dx = 1/32,
-    1/48) cuts the residual per outer iteration more than the plain Jacobi
-    V-cycles on a surface it never saw (unit sphere, dx = 1/64): the judge keeps
-    it, and its mean reduction factor is below Jacobi's reference factor."""
+    """The network trained on residuals of seeded ellipsoids and tori (dx = 1/64)
+    through cpm_mlp_train cuts the residual per outer iteration of the mixed
+    solve more than the plain Jacobi V-cycles on a surface it never saw: the
+    unit sphere at dx = 1/256 (6.8 M points).  The judge keeps it, and its mean
+    and worst reduction factors are below Jacobi's reference factor."""
     torch, pkg = require_cuda()
     from paper_1307_4354_gb300 import train as tr
-    sets = tr.training_set(seed=0, spacings=(1 / 32, 1 / 48))
+    sets = tr.training_set(seed=0, spacings=(1 / 64,))
     sm = pkg.Smoother(0)
     rep_t = tr.train(sm, sets, steps=400, lr=2e-3, lr_final=2e-4)
-    assert rep_t["loss_last"] < rep_t["loss_first"]
-    g = pkg.Band("sphere", (), 1 / 64)
+    assert rep_t["loss_last"] < 0.05 * rep_t["loss_first"], rep_t
+    del sets
+    g = pkg.Band("sphere", (), 1 / 256)
     H = pkg.Hierarchy(g, coarsest_dx=1 / 8, residual="plain")
     _, cp, _ = g.export()
-    _, f = synth.sphere_harmonics(cp[: g.nb], seed=9)
+    _, f = synth.sphere_harmonics(cp[: g.nb])
     H.set_smoother(sm)
     _, rep = H.solve(torch.from_numpy(f).cuda(), tol=1e-10, mode="mixed", learned=True,
                      inner_cycles=3, max_iter=60)
     assert rep["converged"] and not rep["fallback"], rep
-    assert rep["learned_factor"] < rep["jacobi_factor"], (rep["learned_factor"], rep["jacobi_factor"])
+    assert rep["learned_worst"] < rep["jacobi_factor"], (rep["learned_worst"], rep["jacobi_factor"])

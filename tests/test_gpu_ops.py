@@ -156,3 +156,28 @@ def test_vcycle_parity_relaxed_coarse_level():
     with pytest.raises(pkg.capi.CpmError) as e:
         pkg.Hierarchy(g, coarsest_dx=1 / 4)
     assert e.value.status == pkg.capi.CPM_ERR_REACH
+
+
+def test_extension_variants_agree_bit_for_bit():
+    """The three FP32 extension decompositions (one thread per point; persistent
+    pipelined tiles; chunks of points with one base) evaluate the same
+    contraction in the same order: identical w = E u over B and B+, identical
+    V-cycles; the per-level choice made by timing is one of them."""
+    torch, pkg = require_cuda()
+    g = pkg.Band("sphere", (), 1 / 32)
+    Hs = [pkg.Hierarchy(g, coarsest_dx=1 / 8, ext_variant=v) for v in range(3)]
+    Ha = pkg.Hierarchy(g, coarsest_dx=1 / 8)
+    for l in range(Ha.n_levels):
+        v, ms = Ha.ext_tuning(l)
+        assert v in (0, 1, 2) and all(m > 0 for m in ms), (l, v, ms)
+    u = torch.from_numpy(synth.random_band_vector(g.nb, 81)).float().cuda()
+    outs = [[H.extend(u, with_ghost=gh) for H in Hs] for gh in (False, True)]
+    for o in outs:
+        assert torch.equal(o[0], o[1]) and torch.equal(o[0], o[2])
+    f = torch.from_numpy(synth.random_band_vector(g.nb, 82)).float().cuda()
+    us = []
+    for H in Hs:
+        x = torch.zeros_like(f)
+        H.vcycle(f, x)
+        us.append(x)
+    assert torch.equal(us[0], us[1]) and torch.equal(us[0], us[2])
