@@ -304,10 +304,12 @@ def run_cpm(args, world, rank, local):
     with ClockSampler(local) as clk:
         barrier()
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("timed_mixed")  # the range a launch-list capture selects
         ev0.record(st)
         reps = [solve("mixed") for _ in range(args.steps)]
         ev1.record(st)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         barrier()
     mixed_ms = ev0.elapsed_time(ev1) / args.steps
     launches = pkg.capi.cpm_kernel_launches() - launches0
@@ -592,31 +594,59 @@ def run_batch(args, world, rank, local):
 
 def run_micro(args):
     """Kernel micro-benchmark on the dx = 1/256 sphere band (also the ncu target):
-    the extension over B+ in FP32 and FP64 and the operator M (extension +
-    stencil), each timed with CUDA events on the launching stream."""
+    each case is one kind of launch, timed with CUDA events on the launching
+    stream after `--warmup` untimed launches.  Cases: extend32 / extend64 (the
+    extension over B+), extend32_v0 / _v1 / _v2 (the FP32 extension forced to
+    one work decomposition), apply32 / apply64 (M u), jacobi32 (one Jacobi
+    sweep), resid64 (the FP64 relative-form outer residual), vcycle32 (one FP32
+    V-cycle: transfers and the coarsest solve included), mlp (the learned
+    smoother's forward over B)."""
     import torch
 
     import paper_1307_4354_gb300 as pkg
 
     pkg.build()
     band = pkg.Band("sphere", (), DX)
-    H = pkg.Hierarchy(band, coarsest_dx=2 * DX, coarse_sweeps=1)
     nb, ng = band.nb, band.ng
+    wanted = args.micro.split(",")
+    hiers = {}
+
+    def hier(v=None):
+        if v not in hiers:
+            hiers[v] = pkg.Hierarchy(band, coarsest_dx=1 / 8, nu1=args.nu, nu2=args.nu,
+                                     omega=args.omega, residual=args.residual, ext_variant=v)
+        return hiers[v]
+
     g = torch.Generator(device="cuda").manual_seed(0)
     u64 = torch.rand(nb, dtype=torch.float64, device="cuda", generator=g) * 2 - 1
     u32 = u64.float()
+    f64 = torch.rand(nb, dtype=torch.float64, device="cuda", generator=g) * 2 - 1
+    f32 = f64.float()
     w64 = torch.empty(nb + ng, dtype=torch.float64, device="cuda")
     w32 = torch.empty(nb + ng, dtype=torch.float32, device="cuda")
     m64 = torch.empty_like(u64)
     m32 = torch.empty_like(u32)
-    st = torch.cuda.current_stream()
-    cases = {"extend32": lambda: H.extend(u32, with_ghost=True, out=w32),
-             "extend64": lambda: H.extend(u64, with_ghost=True, out=w64),
-             "apply32": lambda: H.apply(u32, out=m32),
-             "apply64": lambda: H.apply(u64, out=m64)}
+    z32 = torch.zeros_like(u32)
+    cases = {
+        "extend32": lambda: hier().extend(u32, with_ghost=True, out=w32),
+        "extend64": lambda: hier().extend(u64, with_ghost=True, out=w64),
+        "extend32_v0": lambda: hier(0).extend(u32, with_ghost=True, out=w32),
+        "extend32_v1": lambda: hier(1).extend(u32, with_ghost=True, out=w32),
+        "extend32_v2": lambda: hier(2).extend(u32, with_ghost=True, out=w32),
+        "apply32": lambda: hier().apply(u32, out=m32),
+        "apply64": lambda: hier().apply(u64, out=m64),
+        "jacobi32": lambda: hier().smooth(f32, u32, sweeps=1),
+        "resid64": lambda: hier().residual(f64, u64, out=m64),
+        "vcycle32": lambda: hier().vcycle(f32, z32.zero_()),
+    }
+    if "mlp" in wanted or args.micro == "all":
+        sm = pkg.Smoother(0)
+        hier().set_smoother(sm)
+        cases["mlp"] = lambda: hier().smoother_correction(f32, out=m32)
     out = {}
+    st = torch.cuda.current_stream()
     for name, fn in cases.items():
-        if args.micro != "all" and args.micro != name:
+        if args.micro != "all" and name not in wanted:
             continue
         for _ in range(args.warmup):
             fn()
@@ -627,8 +657,9 @@ def run_micro(args):
             fn()
         e1.record(st)
         torch.cuda.synchronize()
-        out[name + "_ms"] = e0.elapsed_time(e1) / args.steps
-    print(json.dumps({"micro": out, "nb": nb, "ng": ng}), flush=True)
+        out[name + "_ms"] = e0.elapsed_time(e1) / max(1, args.steps)
+    tuning = [hier().ext_tuning(l) for l in range(hier().n_levels)]
+    print(json.dumps({"micro": out, "nb": nb, "ng": ng, "ext_tuning": tuning}), flush=True)
 
 
 def main():
@@ -652,7 +683,9 @@ def main():
     ap.add_argument("--batch-count", type=int, default=64, help="ellipsoids in the batched workload")
     ap.add_argument("--omega", type=float, default=0.8, help="Jacobi weight")
     ap.add_argument("--micro", default=None,
-                    help="kernel micro-benchmark instead of the solve: extend32|extend64|apply32|apply64|all")
+                    help="kernel micro-benchmark instead of the solve: a comma-separated list of "
+                         "extend32, extend64, extend32_v0/_v1/_v2, apply32, apply64, jacobi32, "
+                         "resid64, vcycle32, mlp, or all")
     args = ap.parse_args()
     world, rank, local = dist_setup()
     if args.micro:

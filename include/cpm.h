@@ -176,7 +176,8 @@ typedef struct cpm_mg_opts {
                              inverse, FP64 (Gauss-Jordan) up to coarse_f64_max
                              points, FP32 (library LU at setup, two FP64
                              refinement steps in FP64 V-cycles) up to
-                             coarse_dense_max, else 40 Jacobi sweeps;
+                             coarse_dense_max, else restarted GMRES(30)
+                             (coarse_gmres restarts);
                              > 0 = that many Jacobi sweeps                      */
   int32_t coarse_f64_max;   /* 0: 16384 (the FP64 inverse costs 8 n^2 bytes)   */
   int32_t coarse_dense_max; /* 0: 40000 (the FP32 inverse costs 4 n^2 bytes);
@@ -206,6 +207,11 @@ typedef struct cpm_mg_opts {
                                u - u_ref per tile, differences formed from
                                exact inputs), which lowers the FP32 rounding
                                floor of the FP32 V-cycle; 0 = the direct form  */
+  int32_t coarse_gmres;     /* restarts of the GMRES(30) coarsest solve used
+                               above coarse_dense_max (0: 3): right-
+                               preconditioned by omega / diag(A), classical
+                               Gram-Schmidt twice, fixed step counts, all on
+                               the device                                      */
   int32_t ext_variant;      /* FP32 extension work decomposition of every level
                                (see cpm_hier_ext_tuning): 0 = chosen per level
                                by timing when the hierarchy is built; 1, 2, 3 =

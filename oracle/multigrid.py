@@ -70,6 +70,7 @@ class MGOptions:
     p: int = 3
     residual: str = "extended"        # "extended": f - A(E u) (Sec. 4.4); "plain": f - A u
     coarse_sweeps: int = 0            # > 0: coarsest level by Jacobi sweeps instead of LU
+    coarse_gmres: int = 0             # > 0: coarsest level by that many restarts of GMRES(30)
     operator: str = "mbr"             # "mbr": diag(L) + (L - diag L) E (Eq. 2.10);
                                       # "paper": E_1 L_band - gamma (I - E_3) (Eq. 3.3)
     cycle: int = 1                    # coarse-grid corrections per level: 1 V-cycle, 2 W-cycle
@@ -134,7 +135,7 @@ def build_hierarchy(surface: Surface, dx: float, coarsest_dx: float, c=1.0,
         lev.diagA = lev.c - lev.ops.diag_M()
     hier = Hierarchy(levels, opts)
     last = levels[-1]
-    if opts.coarse_sweeps == 0:
+    if opts.coarse_sweeps == 0 and opts.coarse_gmres == 0:
         hier.lu = sla.lu_factor(last.ops.A_matrix(last.c).toarray())
     return hier
 
@@ -173,8 +174,58 @@ def transfer_residual(hier: Hierarchy, l: int, u: np.ndarray, f: np.ndarray) -> 
     return f - lev.ops.apply_A(wb, lev.c)
 
 
+GMRES_M = 30
+
+
+def gmres(A, b: np.ndarray, P: np.ndarray, m: int, restarts: int) -> np.ndarray:
+    """Restarted GMRES(m) for A x = b from x = 0, right-preconditioned by
+    diag(P): each cycle builds an orthonormal basis of the Krylov space of
+    A diag(P) from r = b - A x (classical Gram-Schmidt applied twice), reduces
+    the Hessenberg matrix with Givens rotations and adds diag(P) V y, y the
+    least-squares minimiser of ||beta e_1 - H y|| (Saad and Schultz's
+    algorithm; a fixed number of steps, no early exit)."""
+    n = b.size
+    x = np.zeros(n)
+    for _ in range(restarts):
+        r = b - A @ x
+        beta = np.linalg.norm(r)
+        V = np.zeros((m + 1, n))
+        H = np.zeros((m + 1, m))
+        if beta == 0.0:
+            break
+        V[0] = r / beta
+        g = np.zeros(m + 1)
+        g[0] = beta
+        cs, sn = np.zeros(m), np.zeros(m)
+        for j in range(m):
+            w = A @ (P * V[j])
+            for _ in range(2):
+                h = V[: j + 1] @ w
+                w = w - V[: j + 1].T @ h
+                H[: j + 1, j] += h
+            H[j + 1, j] = np.linalg.norm(w)
+            V[j + 1] = w / H[j + 1, j] if H[j + 1, j] > 1e-300 else 0.0
+            for i in range(j):
+                a, bb = H[i, j], H[i + 1, j]
+                H[i, j] = cs[i] * a + sn[i] * bb
+                H[i + 1, j] = -sn[i] * a + cs[i] * bb
+            a, bb = H[j, j], H[j + 1, j]
+            rr = np.hypot(a, bb)
+            cs[j], sn[j] = (a / rr, bb / rr) if rr > 0 else (1.0, 0.0)
+            H[j, j], H[j + 1, j] = rr, 0.0
+            g[j + 1] = -sn[j] * g[j]
+            g[j] = cs[j] * g[j]
+        y = np.linalg.solve(np.triu(H[:m, :m]), g[:m])
+        x = x + P * (V[:m].T @ y)
+    return x
+
+
 def coarse_solve(hier: Hierarchy, f: np.ndarray) -> np.ndarray:
     o = hier.opts
+    if o.coarse_gmres > 0:
+        last = hier.levels[-1]
+        A = last.ops.A_matrix(last.c)
+        return gmres(A, f, o.omega / last.diagA, GMRES_M, o.coarse_gmres)
     if o.coarse_sweeps > 0:
         last = hier.levels[-1]
         u = np.zeros_like(f)

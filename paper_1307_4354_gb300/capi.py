@@ -39,7 +39,8 @@ class cpm_mg_opts(C.Structure):
                 ("c", C.c_double), ("c_device", C.c_void_p), ("residual_mode", C.c_int32),
                 ("coarse_sweeps", C.c_int32), ("coarse_f64_max", C.c_int32),
                 ("coarse_dense_max", C.c_int32), ("op_form", C.c_int32), ("cycle", C.c_int32),
-                ("a_device", C.c_void_p), ("relative", C.c_int32), ("ext_variant", C.c_int32)]
+                ("a_device", C.c_void_p), ("relative", C.c_int32), ("coarse_gmres", C.c_int32),
+                ("ext_variant", C.c_int32)]
 
 
 class cpm_solve_opts(C.Structure):

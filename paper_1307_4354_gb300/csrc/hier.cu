@@ -8,6 +8,7 @@
 #include <string>
 #include <vector>
 
+#include "gmres.cuh"
 #include "mlp.cuh"
 
 namespace cpm {
@@ -213,6 +214,8 @@ struct Workspace {
   cpm::DBuf<double> u_own, f_own, r64, d64;
   cpm::DBuf<double> refv;   // per point of the finest B+: the extension's reference value
   cpm::DBuf<float> r32, d32;
+  cpm::GmresWork<double> gm64;  // coarsest-level GMRES (coarse mode 3)
+  cpm::GmresWork<float> gm32;
   cudaStream_t hs = nullptr;
   cudaEvent_t ev = nullptr;
   // graphs of one outer step: FP64, mixed, mixed with the learned smoother
@@ -232,6 +235,9 @@ struct Workspace {
 };
 template <> cpm::Work<double>& Workspace::work<double>(int l) { return w64[l]; }
 template <> cpm::Work<float>& Workspace::work<float>(int l) { return w32[l]; }
+template <typename T> static cpm::GmresWork<T>& gmres_work(Workspace& W);
+template <> cpm::GmresWork<double>& gmres_work<double>(Workspace& W) { return W.gm64; }
+template <> cpm::GmresWork<float>& gmres_work<float>(Workspace& W) { return W.gm32; }
 
 struct cpm_hier_s {
   cpm_surface surface;
@@ -241,8 +247,10 @@ struct cpm_hier_s {
   DBuf<double> Ainv;     // coarse_mode 0: FP64 inverse
   DBuf<float> Ainv32;    // coarse_mode 1: FP32 inverse
   int32_t nc = 0;
-  int32_t coarse_mode = 0;    // 0: FP64 inverse, 1: FP32 inverse (+FP64 refinement), 2: sweeps
+  int32_t coarse_mode = 0;    // 0: FP64 inverse, 1: FP32 inverse (+FP64 refinement), 2: sweeps,
+                              // 3: GMRES
   int32_t coarse_sweeps = 0;
+  int32_t coarse_restarts = 3;
   cpm_mlp mlp = nullptr;
   std::unique_ptr<cpm::MlpLevelData> mlpd;
   bool learned_active = false;
@@ -275,6 +283,11 @@ static void alloc_workspace(const cpm_hier_s& H, Workspace& W, double* norms_slo
   W.refv.alloc(H.L[0].lev->nplus());
   W.r32.alloc(nB0);
   W.d32.alloc(nB0);
+  if (H.coarse_mode == 3) {
+    const int64_t nc = H.L.back().lev->nB;
+    W.gm64.alloc(nc, kGmresMaxM);
+    W.gm32.alloc(nc, kGmresMaxM);
+  }
   CPM_CUDA_TRY(cudaStreamCreateWithFlags(&W.hs, cudaStreamNonBlocking));
   CPM_CUDA_TRY(cudaEventCreateWithFlags(&W.ev, cudaEventDisableTiming));
   CPM_CUDA_TRY(cudaMallocHost(&W.pinned, 8 * sizeof(double)));
@@ -389,7 +402,17 @@ static void coarse_solve(cpm_hier_s* H, Workspace* const* W, int G, const T* con
     return;
   }
   HLevel& lv = H->L[l];
-  const LevelView<T> v = lv.view<T>();
+  if (H->coarse_mode == 3) {
+    for (int g = 0; g < G; ++g) {
+      Workspace& Wg = *W[g];
+      GmresOps<T> op;
+      op.residual = [H, &Wg, l](const T* ff, const T* uu, T* rr, cudaStream_t s2) {
+        level_op<T>(H, Wg, l, LAP_RESID, ff, uu, rr, nullptr, s2);
+      };
+      gmres_solve<T>(op, gmres_work<T>(Wg), f[g], u[g], lv.dA<T>(), H->coarse_restarts, st);
+    }
+    return;
+  }
   for (int g = 0; g < G; ++g) {
     CPM_CUDA_TRY(cudaMemsetAsync(u[g], 0, sizeof(T) * lv.lev->nB, st));
     for (int s = 0; s < H->coarse_sweeps; ++s)
@@ -799,9 +822,10 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
   } else if (cl.nB <= dense_max) {
     H->coarse_mode = 1;
   } else {
-    H->coarse_mode = 2;
-    H->coarse_sweeps = 40;
+    H->coarse_mode = 3;
+    H->coarse_restarts = o.coarse_gmres > 0 ? o.coarse_gmres : 3;
   }
+  CPM_CHECK(o.coarse_gmres >= 0 && o.coarse_gmres <= 1000, CPM_ERR_ARG, "bad coarse_gmres");
   CPM_CHECK(o.residual_mode == 0 || o.residual_mode == 1, CPM_ERR_ARG, "bad residual_mode");
 
   DBuf<int32_t> err(1);

@@ -89,7 +89,7 @@ class Hierarchy:
                  coarse_sweeps: int = 0, coarse_f64_max: int = 0, coarse_dense_max: int = 0,
                  op_form: str = "mbr", transfer_deg: int = 1, cycle: int = 1,
                  a_device: torch.Tensor | None = None, relative: bool = False,
-                 ext_variant: int | None = None, stream=None):
+                 ext_variant: int | None = None, coarse_gmres: int = 0, stream=None):
         o = capi.cpm_mg_opts()
         o.coarsest_dx, o.nu1, o.nu2, o.omega = coarsest_dx, nu1, nu2, omega
         o.smoother, o.transfer_deg, o.c = _SMOOTHERS[smoother], transfer_deg, c
@@ -102,6 +102,7 @@ class Hierarchy:
         o.a_device = _ptr(a_device, torch.float64, band.nb) if a_device is not None else None
         o.relative = int(relative)
         o.ext_variant = 0 if ext_variant is None else int(ext_variant) + 1
+        o.coarse_gmres = coarse_gmres
         o.c_device = _ptr(c_device, torch.float64, band.nb) if c_device is not None else None
         self.band = band
         self.handle = capi.cpm_build_hierarchy(band.handle, o, _stream(stream))

@@ -104,3 +104,28 @@ def test_relative_form_vcycle_parity(kind, params, dx):
         h.vcycle(torch.from_numpy(fs[perm]).float().cuda(), u32)
         errs.append(np.abs(u32.double().cpu().numpy() - ref).max() / np.abs(ref).max())
     assert errs[0] <= 1e-4 and errs[1] <= 1e-4, errs
+
+
+def test_gmres_coarsest_solve_parity():
+    """A coarsest level above the dense limit is solved by restarted GMRES(30)
+    on the device (3 restarts, right-preconditioned by omega / diag(A)): one
+    V-cycle sphere dx = 1/32 -> 1/16 (26,974 coarse points) equals the oracle's
+    cycle with the same GMRES coarsest solve, and the solve converges."""
+    torch, pkg = require_cuda()
+    g = pkg.Band("sphere", (), 1 / 32)
+    H = pkg.Hierarchy(g, coarsest_dx=1 / 16, nu1=3, nu2=3, omega=0.8, residual="plain",
+                      coarse_dense_max=1000, coarse_f64_max=1000)
+    OH = build_hierarchy(oracle_surface("sphere", ()), 1 / 32, 1 / 16,
+                         opts=MGOptions(smoother="jacobi", nu1=3, nu2=3, omega=0.8, residual="plain",
+                                        coarse_gmres=3))
+    perm = perm_gpu_to_oracle(g, OH.fine.band)
+    nb = OH.fine.band.nb
+    f_o = synth.random_band_vector(nb, 54)
+    ref = vcycle(OH, np.zeros(nb), f_o)[perm]
+    u = torch.zeros(nb, dtype=torch.float64, device="cuda")
+    H.vcycle(torch.from_numpy(f_o[perm]).cuda(), u)
+    err = np.abs(u.cpu().numpy() - ref).max() / np.abs(ref).max()
+    assert err <= 1e-9, err
+    for mode in ("f64", "mixed"):
+        _, rep = H.solve(torch.from_numpy(f_o[perm]).cuda(), tol=1e-10, max_iter=60, mode=mode)
+        assert rep["converged"], (mode, rep)

@@ -49,19 +49,18 @@ def test_dziuk_apply_parity():
 def test_dziuk_solve_converges_to_the_closed_form():
     """dx = 1/128 with V-cycles down to dx = 1/64, the coarsest spacing the reach
     0.0957 allows; that level (about 460 k points, too large for a dense solve)
-    is smoothed by 1000 weighted Jacobi sweeps, so the cycle contracts slowly
-    (0.7 to 0.9 per outer iteration).  The residual falls below 1e-4 and the
-    solution approaches u = x1 x2 to the discretisation error at this spacing."""
+    is solved by restarted GMRES(30) on the device.  The residual falls to
+    1e-8 and the solution approaches u = x1 x2 to the discretisation error at
+    this spacing."""
     torch, pkg = require_cuda()
     dx = 1 / 128
     g = pkg.Band("dziuk", (), dx)
-    H = pkg.Hierarchy(g, coarsest_dx=1 / 64, coarse_sweeps=1000, residual="plain")
+    H = pkg.Hierarchy(g, coarsest_dx=1 / 64, residual="plain", coarse_gmres=4)
     assert H.n_levels == 2
     _, cp, _ = g.export()
     uex, f = synth.dziuk_rhs(cp[: g.nb])
-    u, rep = H.solve(torch.from_numpy(f).cuda(), tol=1e-10, max_iter=60, mode="f64",
-                     raise_on_fail=False)
-    h = np.asarray(rep["history"])
-    assert h[-1] < 1e-4 and np.all(h[1:] < h[:-1]), h
+    u, rep = H.solve(torch.from_numpy(f).cuda(), tol=1e-8, max_iter=60, mode="mixed",
+                     inner_cycles=2)
+    assert rep["converged"], rep["history"]
     err = np.abs(u.cpu().numpy() - uex).max() / np.abs(uex).max()
-    assert err < 5e-4, err
+    assert err < 3e-4, err

@@ -163,3 +163,28 @@ def test_vardiff_vcycle_solution_equals_direct_solve():
     assert rep.converged and rep.iters <= 20, rep.iters
     ud = spla.spsolve(fine.ops.A_matrix(1.0).tocsc(), f)
     assert np.abs(u - ud).max() <= 1e-10 * np.abs(ud).max()
+
+
+def test_gmres_coarse_solve_pins():
+    """The oracle's restarted GMRES (coarsest level): with a Krylov dimension at
+    least the system size it is a direct solve; otherwise each restart cannot
+    increase the residual (it minimises over a space containing 0) and the
+    residual falls for a well-conditioned shifted system."""
+    from oracle.multigrid import gmres
+    rng = np.random.default_rng(4)
+    n = 20
+    A = np.eye(n) * 4 + rng.uniform(-1, 1, (n, n)) * 0.3
+    b = rng.uniform(-1, 1, n)
+    P = 1.0 / np.diag(A)
+    x = gmres(A, b, P, m=n, restarts=1)
+    assert np.abs(A @ x - b).max() <= 1e-12 * np.abs(b).max()
+    H = build_hierarchy(circle(), 1 / 32, 1 / 16, opts=MGOptions(smoother="jacobi", coarse_gmres=1))
+    last = H.levels[-1]
+    Ac = last.ops.A_matrix(last.c).tocsr()
+    f = synth.random_band_vector(last.band.nb, 6)
+    res = []
+    for k in (1, 2, 4):
+        xk = gmres(Ac, f, 0.8 / last.diagA, 30, k)
+        res.append(np.abs(Ac @ xk - f).max())
+    assert res[0] < np.abs(f).max() and res[1] <= res[0] and res[2] <= res[1], res
+    assert res[2] < 1e-2 * np.abs(f).max(), res
