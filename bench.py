@@ -31,9 +31,11 @@ sys.path.insert(0, ROOT)
 DX = 1.0 / 256
 METRIC = "s to 1e-10 rel residual, sphere Δx=1/256: FP32-IR/learned vs FP64; HBM GB/s"
 SAMPLE_DX = 1.0 / 64
-# FP64 flops of one extension evaluation per point: the separable 4x4x4
-# contraction, 64 + 16 + 4 multiply-adds (the FP64 weights are precomputed).
-EXTEND_FLOPS = 2 * (64 + 16 + 4)
+# Outer residual in FP32 pairs (cpm_residual): algorithmic bytes per point of
+# B+ (pair weights 96, record 4, delta 8, ref 4) and per point of B (u staged
+# 8; the stencil's neighbour indices 24, u 8, f 8, r 8, own delta and ref 12).
+RESID_PAIR_BYTES_BPLUS = 96 + 4 + 8 + 4
+RESID_PAIR_BYTES_B = 8 + 24 + 8 + 8 + 8 + 12
 # FP32 extension bytes: per point of B+ its record 4 + fractions 12 + w 4; per
 # point of B its value u 4 (the tile tables, ~2 B per point, are not counted).
 EXTEND32_BYTES_BPLUS = 20
@@ -41,7 +43,6 @@ EXTEND32_BYTES_B = 4
 # DRAM bytes (read + write) of one FP32 extension launch over B+ of the unit
 # sphere at dx = 1/256, from one ncu capture of the same kernel and workload.
 EXTEND32_TRAFFIC = 165.8112e6 + 21.328128e6
-FP64_PEAK_TFLOPS = 1.25  # nominal GB300 FP64 rate (no measured FP64 peak is provided)
 
 
 def _sphere_rhs(y):
@@ -415,22 +416,22 @@ def run_cpm(args, world, rank, local):
     torch.cuda.synchronize()
     e2e_ms = ev0.elapsed_time(ev1) / args.steps
 
-    # dominant kernel: FP64 extension over B+ (one launch = nB + nG points), CUDA events
-    # on the launching stream; and the FP32 extension for the memory roofline.
-    w64 = torch.empty(nb + band.ng, dtype=torch.float64, device=dev)
+    # dominant kernel: the FP32 extension over B+ (one launch = nB + nG points),
+    # CUDA events on the launching stream; and the outer residual in FP32 pairs.
     w32 = torch.empty(nb + band.ng, dtype=torch.float32, device=dev)
+    r64 = torch.empty_like(u)
     u32 = u.float()
     for _ in range(3):
-        H.extend(u, with_ghost=True, out=w64)
+        H.residual(f, u, out=r64)
         H.extend(u32, with_ghost=True, out=w32)
     reps_k = 20
     torch.cuda.synchronize()
     ev0.record(st)
     for _ in range(reps_k):
-        H.extend(u, with_ghost=True, out=w64)
+        H.residual(f, u, out=r64)
     ev1.record(st)
     torch.cuda.synchronize()
-    ext64_ms = ev0.elapsed_time(ev1) / reps_k
+    resid_ms = ev0.elapsed_time(ev1) / reps_k
     ev0.record(st)
     for _ in range(reps_k):
         H.extend(u32, with_ghost=True, out=w32)
@@ -438,7 +439,8 @@ def run_cpm(args, world, rank, local):
     torch.cuda.synchronize()
     ext32_ms = ev0.elapsed_time(ev1) / reps_k
     npl = nb + band.ng
-    ach64 = EXTEND_FLOPS * npl / (ext64_ms * 1e-3) / 1e12
+    bytes_res = RESID_PAIR_BYTES_BPLUS * npl + RESID_PAIR_BYTES_B * nb
+    ach_res = bytes_res / (resid_ms * 1e-3) / 1e9
     bytes32 = EXTEND32_BYTES_BPLUS * npl + EXTEND32_BYTES_B * nb
     ach32 = bytes32 / (ext32_ms * 1e-3) / 1e9
     pk = peaks()
@@ -468,6 +470,8 @@ def run_cpm(args, world, rank, local):
                    "l2": "inputs larger than L2 (no flush)",
                    "parallelism": f"replicas x{world}"},
         "iters_mixed": iters_mixed, "fp64_s": f64_ms / 1e3, "iters_fp64": reps64[-1]["iters"],
+        "history_mixed": reps[-1]["history"], "f64_checks": reps[-1]["f64_checks"],
+        "pair_floor": reps[-1]["pair_floor"],
         "accuracy": dict(accuracy, note="max-norm differences relative to max |u_f64| (or |u_exact|)"),
         "learned": learned,
         "band_point_updates_per_s": updates / (mixed_ms * 1e-3),
@@ -484,12 +488,13 @@ def run_cpm(args, world, rank, local):
                      "traffic": EXTEND32_TRAFFIC if wl["kind"] == "sphere" and wl["dx"] == DX else None,
                      "algorithmic_bytes": bytes32, "points": npl, "ms": ext32_ms,
                      "peak_source": "measured copy bandwidth (MEASURED_PEAKS.json)"},
-        "roofline_f64_extend": {"kernel": "k_extend_tiles<double,3> (FP64 extension of the outer "
-                                          "residual)", "bound": "alu",
-                                "achieved": ach64, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                                "frac": ach64 / FP64_PEAK_TFLOPS, "traffic": None,
-                                "flops_per_point": EXTEND_FLOPS, "points": npl, "ms": ext64_ms,
-                                "peak_source": "nominal FP64 rate"},
+        "roofline_outer_residual": {"kernel": "cpm_residual in FP32 pairs (k_extend_pair over B+, "
+                                              "k_resid_pair over B, norms)", "bound": "hbm",
+                                    "achieved": ach_res, "peak": pk.get("hbm_gbs"), "unit": "GB/s",
+                                    "frac": ach_res / pk.get("hbm_gbs", 6800.0), "traffic": None,
+                                    "algorithmic_bytes": bytes_res, "ms": resid_ms,
+                                    "note": "the pair extension is FP32-pipe and latency bound "
+                                            "(pair arithmetic, 72 registers); see profiles"},
         "clocks": clk.summary(),
     }
     if cpu:
@@ -598,9 +603,11 @@ def run_micro(args):
     stream after `--warmup` untimed launches.  Cases: extend32 / extend64 (the
     extension over B+), extend32_v0 / _v1 / _v2 (the FP32 extension forced to
     one work decomposition), apply32 / apply64 (M u), jacobi32 (one Jacobi
-    sweep), resid64 (the FP64 relative-form outer residual), vcycle32 (one FP32
+    sweep), resid64 / resid64_f64 (the relative-form outer residual in FP32 pairs
+    / in FP64), vcycle32 (one FP32
     V-cycle: transfers and the coarsest solve included), mlp (the learned
-    smoother's forward over B)."""
+    smoother's forward over B).  The timed launches sit in the NVTX range
+    "micro", so that ncu can select them with --nvtx-include micro/."""
     import torch
 
     import paper_1307_4354_gb300 as pkg
@@ -611,11 +618,12 @@ def run_micro(args):
     wanted = args.micro.split(",")
     hiers = {}
 
-    def hier(v=None):
-        if v not in hiers:
-            hiers[v] = pkg.Hierarchy(band, coarsest_dx=1 / 8, nu1=args.nu, nu2=args.nu,
-                                     omega=args.omega, residual=args.residual, ext_variant=v)
-        return hiers[v]
+    def hier(v=None, outer_f64=False):
+        if (v, outer_f64) not in hiers:
+            hiers[v, outer_f64] = pkg.Hierarchy(band, coarsest_dx=1 / 8, nu1=args.nu, nu2=args.nu,
+                                                omega=args.omega, residual=args.residual,
+                                                ext_variant=v, outer_f64=outer_f64)
+        return hiers[v, outer_f64]
 
     g = torch.Generator(device="cuda").manual_seed(0)
     u64 = torch.rand(nb, dtype=torch.float64, device="cuda", generator=g) * 2 - 1
@@ -637,6 +645,7 @@ def run_micro(args):
         "apply64": lambda: hier().apply(u64, out=m64),
         "jacobi32": lambda: hier().smooth(f32, u32, sweeps=1),
         "resid64": lambda: hier().residual(f64, u64, out=m64),
+        "resid64_f64": lambda: hier(outer_f64=True).residual(f64, u64, out=m64),
         "vcycle32": lambda: hier().vcycle(f32, z32.zero_()),
     }
     if "mlp" in wanted or args.micro == "all":
@@ -652,11 +661,13 @@ def run_micro(args):
             fn()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("micro")
         e0.record(st)
         for _ in range(args.steps):
             fn()
         e1.record(st)
         torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
         out[name + "_ms"] = e0.elapsed_time(e1) / max(1, args.steps)
     tuning = [hier().ext_tuning(l) for l in range(hier().n_levels)]
     print(json.dumps({"micro": out, "nb": nb, "ng": ng, "ext_tuning": tuning}), flush=True)

@@ -174,7 +174,9 @@ typedef struct cpm_mg_opts {
                              0: f - A (E u) (Sec. 4.4), 1: f - A u              */
   int32_t coarse_sweeps;  /* coarsest level: 0 = direct solve by an explicit
                              inverse, FP64 (Gauss-Jordan) up to coarse_f64_max
-                             points, FP32 (library LU at setup, two FP64
+                             points (FP32 V-cycles multiply by its FP32
+                             rounding when it has at most 8192), FP32
+                             (library LU at setup, two FP64
                              refinement steps in FP64 V-cycles) up to
                              coarse_dense_max, else restarted GMRES(30)
                              (coarse_gmres restarts);
@@ -216,6 +218,11 @@ typedef struct cpm_mg_opts {
                                (see cpm_hier_ext_tuning): 0 = chosen per level
                                by timing when the hierarchy is built; 1, 2, 3 =
                                variant 0, 1, 2 everywhere                       */
+  int32_t outer_f64;        /* CPM_OP_MBR: arithmetic of the outer residual
+                               (cpm_residual, cpm_solve, cpm_solve_batch):
+                               0 = FP32 pairs (about 48 significand bits, see
+                               cpm_residual), 1 = FP64.  Other forms: ignored
+                               (their residual is FP64, direct form)            */
 } cpm_mg_opts;
 
 typedef enum cpm_op_form { CPM_OP_MBR = 0, CPM_OP_PAPER = 1, CPM_OP_VARDIFF = 2 } cpm_op_form;
@@ -426,27 +433,46 @@ typedef struct cpm_solve_report {
   double jacobi_factor;        /* reference reduction factor (Jacobi)         */
   double learned_factor;       /* mean reduction factor with the network      */
   double learned_worst;        /* largest reduction factor with the network   */
+  int32_t f64_checks;          /* outer residuals in FP32 pairs checked in FP64
+                                  (see cpm_solve)                             */
+  double pair_floor;           /* last estimate of the pair residual's rounding
+                                  error relative to ||f||_inf (0: FP64 only)  */
 } cpm_solve_report;
 
 /*
  * Solve A u = f on the finest level.  f, u: FP64 device vectors of length
- * |B_0|; u holds the initial guess unless zero_init.  The outer residual and
- * the solution accumulator are FP64 in both modes.  Synchronous (reads one
- * residual norm per outer iteration).  report may be NULL.
+ * |B_0|; u holds the initial guess unless zero_init.  The solution accumulator
+ * is FP64 in both modes; the outer residual is evaluated as cpm_residual
+ * (FP32 pairs unless outer_f64).  With pairs, the residual also yields an
+ * estimate of its rounding error (4 x 2^-48 max|u - u_ref| 6d / dx^2, about
+ * ten times the measured error); a pair residual that meets the tolerance only
+ * within that estimate, or has reached it, or has stopped falling (at most
+ * halved by an outer iteration), is checked by the FP64 evaluation of the
+ * same iterate, and if that check misses the tolerance the rest of the solve
+ * uses FP64 residuals.  Synchronous (reads the residual norms once per outer
+ * iteration).  report may be NULL.
  * Errors: CPM_ERR_NOT_CONVERGED, CPM_ERR_DIVERGED (u holds the last iterate).
  */
 cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opts* opts,
                      cpm_solve_report* report, cpm_stream stream);
 
 /*
- * r = f - A u on the finest level in FP64 (the outer residual of cpm_solve,
- * difference form of M, Eq. 2.10).  Evaluated in relative form: the
- * extension of each tile works on u - u_ref (u_ref = u at one band node of
- * the tile) and the stencil combines reference differences and extension
- * differences formed from exact inputs, so the rounding error scales with
- * local differences of u rather than |u|/dx^2 (the plain form has a relative
- * floor near 1e-10 at dx = 1/512).  f, u, r: FP64 device vectors of length
- * |B_0|.  cpm_residual_norms uses the same evaluation.
+ * r = f - A u on the finest level (the outer residual of cpm_solve,
+ * difference form of M, Eq. 2.10), FP64 inputs and output.  Evaluated in
+ * relative form: the extension of each tile works on u - u_ref (u_ref = u at
+ * one band node of the tile) and the stencil combines reference differences
+ * and extension differences formed from exact inputs, so the rounding error
+ * scales with local differences of u rather than |u|/dx^2 (the plain form has
+ * a relative floor near 1e-10 at dx = 1/512).  With outer_f64 = 0 (CPM_OP_MBR,
+ * the default) the reference is rounded to float, u - u_ref is formed in FP64
+ * and split into a pair of floats, and the extension and the stencil sums
+ * run in FP32-pair arithmetic (exact products by fused multiply-add, TwoSum
+ * for the leading parts: about 48 significand bits) on the FP32 pipe; the
+ * term u_ref - u, the scaling by 1/dx^2 and the last sums are FP64.  Its
+ * relative floor grows like 1/dx, about 4e-12 at dx = 1/512 on the unit sphere
+ * against 1e-12 for the FP64 form.  Other operator forms evaluate r in FP64,
+ * direct form.  f, u, r: FP64 device vectors of length |B_0|.
+ * cpm_residual_norms uses the same evaluation.
  */
 cpm_status cpm_residual(cpm_hier h, const double* f, const double* u, double* r, cpm_stream stream);
 

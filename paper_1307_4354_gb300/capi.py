@@ -40,7 +40,8 @@ class cpm_mg_opts(C.Structure):
                 ("coarse_sweeps", C.c_int32), ("coarse_f64_max", C.c_int32),
                 ("coarse_dense_max", C.c_int32), ("op_form", C.c_int32), ("cycle", C.c_int32),
                 ("a_device", C.c_void_p), ("relative", C.c_int32), ("coarse_gmres", C.c_int32),
-                ("ext_variant", C.c_int32)]
+                ("ext_variant", C.c_int32),
+                ("outer_f64", C.c_int32)]
 
 
 class cpm_solve_opts(C.Structure):
@@ -54,7 +55,7 @@ class cpm_solve_report(C.Structure):
                 ("history", C.c_double * CPM_MAX_HISTORY), ("seconds", C.c_double),
                 ("learned_iters", C.c_int32), ("fallback", C.c_int32),
                 ("jacobi_factor", C.c_double), ("learned_factor", C.c_double),
-                ("learned_worst", C.c_double)]
+                ("learned_worst", C.c_double), ("f64_checks", C.c_int32), ("pair_floor", C.c_double)]
 
 
 CPM_MLP_NPARAMS = 6337

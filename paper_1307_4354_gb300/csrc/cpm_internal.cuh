@@ -177,6 +177,7 @@ struct Level {
   DBuf<uint32_t> erec;        // band index << 6 | stencil base inside the brick
   DBuf<float> efr32;          // d x (nB+nG) fractions in E order
   DBuf<double> ew64;          // 4d x (nB+nG) FP64 cubic weights in E order
+  DBuf<float2> ewp;           // the same as FP32 pairs (built on demand: build_pair_weights)
   // chunks: runs of at most kChunkMax consecutive E-order points of one tile
   // that share one stencil base (and are all in B or all in G); one thread
   // loads the base's 4^d values once and evaluates every point of the chunk
@@ -205,6 +206,8 @@ void build_level(const cpm_surface& s, double lo, double dx, int n, double lambd
 void band_counts(const Level& L, cudaStream_t st, int64_t counts[4]);
 // Group the points of a level into extension tiles (ext.cu).
 void build_ext_tiles(Level& L, cudaStream_t st);
+// L.ewp from L.ew64 (each weight split into a float pair, see pair.cuh).
+void build_pair_weights(Level& L, cudaStream_t st);
 
 // Host counter of solve-path kernel launches (cpm_kernel_launches).  While a
 // stream capture is being recorded the launch helpers do not count; a graph

@@ -16,6 +16,7 @@
 #include <algorithm>
 
 #include "ops.cuh"
+#include "pair.cuh"
 
 namespace cpm {
 
@@ -445,54 +446,80 @@ struct TileBox {
   int32_t start[NB][2];
 };
 
+// Box row r of a tile (box rows run over y fastest, then z): its position,
+// the x range of its windows, and the band indices of its first node in each
+// of the two bricks it crosses (band nodes of a brick row are consecutive, so
+// one popcount per brick gives the start).  False if r is past the last row.
+struct BoxRow {
+  int y, z, xlo, xhi;
+  uint32_t rba, rbb;  // occupancy of the row's 4 nodes in the low / high brick
+  int32_t ca, cb;     // band index of the row's first node at x >= xlo / x >= 4
+};
+template <int NB>
+__device__ __forceinline__ bool box_row(const uint32_t (&mask)[NB][2], const int32_t (&start)[NB][2],
+                                        uint32_t tbox, int dim, int r, BoxRow& b) {
+  b.xlo = tbox & 3;
+  b.xhi = (tbox >> 2) & 3;
+  const int ylo = (tbox >> 4) & 3, yhi = (tbox >> 6) & 3;
+  const int zlo = dim == 3 ? (tbox >> 8) & 3 : 0, zhi = dim == 3 ? ((tbox >> 10) & 3) + 3 : 0;
+  const int ny = yhi + 4 - ylo;
+  if (r >= ny * (zhi + 1 - zlo)) return false;
+  b.y = ylo + r % ny;
+  b.z = zlo + r / ny;
+  const int jyz = ((b.y >> 2) << 1) | ((b.z >> 2) << 2);
+  const int half = (b.z >> 1) & 1;
+  const int shift = ((b.y & 3) << 2) | ((b.z & 1) << 4);
+  const uint32_t wa = mask[jyz][half], wb = mask[jyz | 1][half];
+  b.rba = (wa >> shift) & 0xFu;
+  b.rbb = (wb >> shift) & 0xFu;
+  const uint32_t below = (1u << shift) - 1u;
+  b.ca = start[jyz][half] + __popc(wa & below) + __popc(b.rba & ((1u << b.xlo) - 1u));
+  b.cb = start[jyz | 1][half] + __popc(wb & below);
+  return true;
+}
+
+// The tile's brick masks and band starts into shared memory (threads < NB).
+template <int NB>
+__device__ __forceinline__ void load_box_bricks(const uint64_t* tile_mask, const int32_t* tile_bstart,
+                                                int32_t tile, uint32_t (&mask)[NB][2],
+                                                int32_t (&start)[NB][2]) {
+  if (threadIdx.x < NB) {
+    const int j = threadIdx.x;
+    const uint64_t m = __ldg(tile_mask + 8 * (int64_t)tile + j);
+    const int32_t s0 = __ldg(tile_bstart + 8 * (int64_t)tile + j);
+    mask[j][0] = (uint32_t)m;
+    mask[j][1] = (uint32_t)(m >> 32);
+    start[j][0] = s0;
+    start[j][1] = s0 + __popc((uint32_t)m);
+  }
+}
+
 template <typename T, int DIM, bool REL, int NT>
 __device__ __forceinline__ T stage_box(const LevelView<T>& L, const T* __restrict__ u, int32_t tile,
                                        uint32_t tbox, TileBox<T, DIM, REL>& sm) {
   constexpr int RS = TileBox<T, DIM, REL>::RS;
-  constexpr int NB = TileBox<T, DIM, REL>::NB;
-  if (threadIdx.x < NB) {
-    const int j = threadIdx.x;
-    const uint64_t m = __ldg(L.tile_mask + 8 * (int64_t)tile + j);
-    const int32_t s0 = __ldg(L.tile_bstart + 8 * (int64_t)tile + j);
-    sm.mask[j][0] = (uint32_t)m;
-    sm.mask[j][1] = (uint32_t)(m >> 32);
-    sm.start[j][0] = s0;
-    sm.start[j][1] = s0 + __popc((uint32_t)m);
-  }
+  load_box_bricks(L.tile_mask, L.tile_bstart, tile, sm.mask, sm.start);
   __syncthreads();
   const T ref = REL ? __ldg(u + sm.start[0][0]) : T(0);
-  const int xlo = tbox & 3, xhi = (tbox >> 2) & 3;
-  const int ylo = (tbox >> 4) & 3, yhi = (tbox >> 6) & 3;
-  const int zlo = DIM == 3 ? (tbox >> 8) & 3 : 0, zhi = DIM == 3 ? ((tbox >> 10) & 3) + 3 : 0;
-  const int ny = yhi + 4 - ylo;
-  const int nrows = ny * (zhi + 1 - zlo);
-  for (int r = threadIdx.x; r < nrows; r += NT) {
-    const int y = ylo + r % ny, z = zlo + r / ny;
-    const int jyz = ((y >> 2) << 1) | ((z >> 2) << 2);
-    const int half = (z >> 1) & 1;
-    const int shift = ((y & 3) << 2) | ((z & 1) << 4);
-    const uint32_t wa = sm.mask[jyz][half], wb = sm.mask[jyz | 1][half];
-    const uint32_t rba = (wa >> shift) & 0xFu, rbb = (wb >> shift) & 0xFu;
-    const uint32_t below = (1u << shift) - 1u;
-    int32_t ca = sm.start[jyz][half] + __popc(wa & below) + __popc(rba & ((1u << xlo) - 1u));
-    int32_t cb = sm.start[jyz | 1][half] + __popc(wb & below);
+  BoxRow b;
+  for (int r = threadIdx.x; box_row(sm.mask, sm.start, tbox, DIM, r, b); r += NT) {
     T v[7];
 #pragma unroll
     for (int i = 0; i < 7; ++i) {
-      const int x = xlo + i;
+      const int x = b.xlo + i;
       v[i] = T(0);
-      if (x <= xhi + 3) {
+      if (x <= b.xhi + 3) {
         const bool hi = x >= 4;
-        if (((hi ? rbb : rba) >> (x & 3)) & 1u) {
-          v[i] = __ldg(u + (hi ? cb++ : ca++));
+        if (((hi ? b.rbb : b.rba) >> (x & 3)) & 1u) {
+          v[i] = __ldg(u + (hi ? b.cb++ : b.ca++));
           if (REL) v[i] -= ref;
         }
       }
     }
-    T* row = sm.win + (z * 7 + y) * RS;
+    T* row = sm.win + (b.z * 7 + b.y) * RS;
 #pragma unroll
     for (int i = 0; i < 4; ++i)
-      if (xlo + i <= xhi) store4(row + 4 * (xlo + i), v[i], v[i + 1], v[i + 2], v[i + 3]);
+      if (b.xlo + i <= b.xhi) store4(row + 4 * (b.xlo + i), v[i], v[i + 1], v[i + 2], v[i + 3]);
   }
   __syncthreads();
   return ref;
@@ -531,6 +558,160 @@ __global__ void __launch_bounds__(kExtThreads) k_extend_tiles(LevelView<T> L, co
     if (kn < end) {
       rec = __ldg(L.erec + kn);
       pw.load(L, kn);
+    }
+  }
+}
+
+// ------------------------------------------------- relative form in FP32 pairs
+// The outer residual's extension (the relative form of the FP64 kernel above)
+// evaluated in FP32-pair arithmetic (pair.cuh) on the FP32 pipe.  Per tile the
+// reference is ref = u at the last band node of the tile's base brick (the
+// brick holding its points' stencil bases, box brick 0, which holds at least
+// those bases), rounded to float, so that reference differences are exact in
+// pairs; the box is staged as d = u - ref (one FP64 subtraction per node),
+// split into hi and lo planes.  Per point the 4^d contraction runs in pairs,
+// y for each (z, x) with two x positions per packed instruction, then z, then
+// x, with the 1-D weights split into pairs when the level was built.  Output:
+// delta_j = (E u)_j - ref_j as a pair and ref_j, for every point of B+.
+template <int DIM>
+struct PairBox {
+  static constexpr int NZ = DIM == 3 ? 7 : 1;
+  static constexpr int NB = DIM == 3 ? 8 : 4;
+  __align__(16) float hi[NZ * 7 * kRS];
+  __align__(16) float lo[NZ * 7 * kRS];
+  uint32_t mask[NB][2];
+  int32_t start[NB][2];
+  uint32_t dmax;  // largest |hi| staged (float bits)
+};
+
+template <int DIM>
+__device__ __forceinline__ float stage_box_pair(const LevelView<double>& L, const double* __restrict__ u,
+                                                int32_t tile, uint32_t tbox, PairBox<DIM>& sm) {
+  load_box_bricks(L.tile_mask, L.tile_bstart, tile, sm.mask, sm.start);
+  if (threadIdx.x == 0) sm.dmax = 0u;
+  __syncthreads();
+  // brick 0 holds the tile's stencil bases, which are band nodes (checked when
+  // the band is built); the clamp only keeps the index inside B regardless
+  const int32_t last = min(max(sm.start[0][1] + __popc(sm.mask[0][1]) - 1, 0), L.nB - 1);
+  const float ref = (float)__ldg(u + last);
+  const double refd = (double)ref;
+  float amax = 0.f;
+  BoxRow b;
+  for (int r = threadIdx.x; box_row(sm.mask, sm.start, tbox, DIM, r, b); r += kExtThreads) {
+    float vh[7], vl[7];
+#pragma unroll
+    for (int i = 0; i < 7; ++i) {
+      const int x = b.xlo + i;
+      vh[i] = vl[i] = 0.f;
+      if (x <= b.xhi + 3) {
+        const bool hi = x >= 4;
+        if (((hi ? b.rbb : b.rba) >> (x & 3)) & 1u) {
+          const float2 d = pair_split(__ldg(u + (hi ? b.cb++ : b.ca++)) - refd);
+          vh[i] = d.x;
+          vl[i] = d.y;
+          amax = fmaxf(amax, fabsf(d.x));
+        }
+      }
+    }
+    const int o = (b.z * 7 + b.y) * kRS;
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+      if (b.xlo + i <= b.xhi) {
+        store4(sm.hi + o + 4 * (b.xlo + i), vh[i], vh[i + 1], vh[i + 2], vh[i + 3]);
+        store4(sm.lo + o + 4 * (b.xlo + i), vl[i], vl[i + 1], vl[i + 2], vl[i + 3]);
+      }
+  }
+  uint32_t am = __float_as_uint(amax);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) am = max(am, __shfl_xor_sync(0xffffffffu, am, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(&sm.dmax, am);
+  __syncthreads();
+  return ref;
+}
+
+// The pair contraction of one point from the windows at offset o.
+template <int DIM>
+__device__ __forceinline__ void contract_pair(const PairBox<DIM>& sm, int o, const float2 (&w)[3][4],
+                                              float& dh, float& dl) {
+  Pair2 q01{}, q23{};
+#pragma unroll
+  for (int c = 0; c < (DIM == 3 ? 4 : 1); ++c) {
+    Pair2 p01, p23;
+#pragma unroll
+    for (int b = 0; b < 4; ++b) {
+      const int ob = o + (c * 7 + b) * kRS;
+      const float4 xh = *reinterpret_cast<const float4*>(sm.hi + ob);
+      const float4 xl = *reinterpret_cast<const float4*>(sm.lo + ob);
+      const PairW2 wy = pw2(w[1][b]);
+      if (b == 0) {
+        p01 = pmul(wy, make_float2(xh.x, xh.y), make_float2(xl.x, xl.y));
+        p23 = pmul(wy, make_float2(xh.z, xh.w), make_float2(xl.z, xl.w));
+      } else {
+        pmul_acc(wy, make_float2(xh.x, xh.y), make_float2(xl.x, xl.y), p01);
+        pmul_acc(wy, make_float2(xh.z, xh.w), make_float2(xl.z, xl.w), p23);
+      }
+    }
+    if (DIM == 2) {
+      q01 = p01;
+      q23 = p23;
+    } else {
+      const PairW2 wz = pw2(w[2][c]);
+      if (c == 0) {
+        q01 = pmul(wz, p01.h, p01.l);
+        q23 = pmul(wz, p23.h, p23.l);
+      } else {
+        pmul_acc(wz, p01.h, p01.l, q01);
+        pmul_acc(wz, p23.h, p23.l, q23);
+      }
+    }
+  }
+  // x: lanes (0, 1) then (2, 3) into one pair per lane, then the two lanes
+  Pair2 s = pmul(pw2(w[0][0], w[0][1]), q01.h, q01.l);
+  pmul_acc(pw2(w[0][2], w[0][3]), q23.h, q23.l, s);
+  float h, t;
+  two_sum(s.h.x, s.h.y, h, t);
+  const float l = __fadd_rn(__fadd_rn(s.l.x, s.l.y), t);
+  fast_two_sum(h, l, dh, dl);
+}
+
+template <int DIM>
+#ifndef CPM_PAIR_MINB
+#define CPM_PAIR_MINB 16  // resident CTAs per SM asked of the register allocator
+#endif
+__global__ void __launch_bounds__(kExtThreads, CPM_PAIR_MINB) k_extend_pair(LevelView<double> L, const double* __restrict__ u,
+                                                             float2* __restrict__ delta,
+                                                             float* __restrict__ refv, uint32_t* dmax) {
+  __shared__ PairBox<DIM> sm;
+  const int32_t tile = blockIdx.x;
+  const uint32_t tbox = __ldg(L.tile_box + tile);
+  const int32_t beg = __ldg(L.tile_start + tile), end = __ldg(L.tile_start + tile + 1);
+  if (beg == end) return;
+  const int64_t np = L.nplus;
+  int32_t k = beg + threadIdx.x;
+  uint32_t rec = 0;
+  float2 w[3][4];
+  auto load_w = [&](int32_t kk) {
+#pragma unroll
+    for (int a = 0; a < DIM; ++a)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) w[a][j] = __ldg(L.ewp + (4 * a + j) * np + kk);
+  };
+  if (k < end) {
+    rec = __ldg(L.erec + k);
+    load_w(k);
+  }
+  const float ref = stage_box_pair<DIM>(L, u, tile, tbox, sm);
+  if (threadIdx.x == 0) atomicMax(dmax + (tile & (kPairSlots - 1)), sm.dmax);
+  for (; k < end; k += kExtThreads) {
+    const int o = ((rec >> 4) & 3) * 7 * kRS + ((rec >> 2) & 3) * kRS + (rec & 3) * 4;
+    float dh, dl;
+    contract_pair<DIM>(sm, o, w, dh, dl);
+    delta[rec >> 6] = make_float2(dh, dl);
+    refv[rec >> 6] = ref;
+    const int32_t kn = k + kExtThreads;
+    if (kn < end) {
+      rec = __ldg(L.erec + kn);
+      load_w(kn);
     }
   }
 }
@@ -833,6 +1014,30 @@ void launch_extend_rel(const LevelView<T>& L, const T* u, T* delta, T* refv, cud
     k_extend_tiles<T, 2, true><<<nt, kExtThreads, 0, st>>>(L, u, delta, true, refv);
   count_launch();
 }
+__global__ void k_pair_weights(const double* w, float2* wp, int64_t n) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) wp[q] = pair_split(w[q]);
+}
+
+void build_pair_weights(Level& L, cudaStream_t st) {
+  const int64_t n = (int64_t)4 * L.dim * L.nplus();
+  L.ewp.alloc((size_t)n);
+  if (n > 0) k_pair_weights<<<nblk(n, 256), 256, 0, st>>>(L.ew64.get(), L.ewp.get(), n);
+  CPM_CUDA_TRY(cudaGetLastError());
+}
+
+void launch_extend_pair(const LevelView<double>& L, const double* u, float2* delta, float* refv,
+                        uint32_t* dmax, cudaStream_t st) {
+  const int32_t nt = L.ntiles;
+  if (nt <= 0) return;
+  CPM_CHECK(L.ewp != nullptr, CPM_ERR_ARG, "pair weights not built");
+  if (L.dim == 3)
+    k_extend_pair<3><<<nt, kExtThreads, 0, st>>>(L, u, delta, refv, dmax);
+  else
+    k_extend_pair<2><<<nt, kExtThreads, 0, st>>>(L, u, delta, refv, dmax);
+  count_launch();
+}
+
 template void launch_extend_rel<double>(const LevelView<double>&, const double*, double*, double*,
                                         cudaStream_t);
 template void launch_extend_rel<float>(const LevelView<float>&, const float*, float*, float*,

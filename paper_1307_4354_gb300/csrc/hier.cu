@@ -64,6 +64,14 @@ __global__ void k_diag_A(const double* diagM, const double* cvec, double cval, d
 #define CPM_TRANSFER_INDEXED 1
 #endif
 
+// dst = src rounded to FP32.
+__global__ void k_round_f32(const double* src, float* dst, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) dst[i] = (float)src[i];
+}
+// Largest coarsest level whose FP64 inverse also gets an FP32 copy (256 MB).
+constexpr int32_t kCoarseF32CopyMax = 8192;
+
 __global__ void k_transfer_index(const uint64_t* base, int32_t n, int dim, BrickView src, int32_t* idx) {
   const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
@@ -141,6 +149,7 @@ LevelView<double> HLevel::view<double>() const {
   v.erec = lev->erec.get();
   v.efr = lev->efr32.get();
   v.ew64 = lev->ew64.get();
+  v.ewp = lev->ewp.get();
   v.ntiles = lev->ntiles;
   v.ext_variant = lev->ext_variant;
   v.echunk = lev->echunk.get();
@@ -169,6 +178,7 @@ LevelView<float> HLevel::view<float>() const {
   v.erec = lev->erec.get();
   v.efr = lev->efr32.get();
   v.ew64 = lev->ew64.get();
+  v.ewp = lev->ewp.get();
   v.ntiles = lev->ntiles;
   v.ext_variant = lev->ext_variant;
   v.echunk = lev->echunk.get();
@@ -212,16 +222,23 @@ struct Workspace {
   double* norms = nullptr;
   cpm::DBuf<double> normf;  // norms of f
   cpm::DBuf<double> u_own, f_own, r64, d64;
-  cpm::DBuf<double> refv;   // per point of the finest B+: the extension's reference value
+  cpm::DBuf<double> refv;   // per point of the finest B+: the extension's reference value (FP64 form)
+  cpm::DBuf<float2> dpair;  // pair form: delta_j = (E u)_j - ref_j over the finest B+
+  cpm::DBuf<float> rpair;   // pair form: ref_j
+  cpm::DBuf<uint32_t> dmax; // pair form: slots of the largest staged |u - ref| (norms[3])
   cpm::DBuf<float> r32, d32;
   cpm::GmresWork<double> gm64;  // coarsest-level GMRES (coarse mode 3)
   cpm::GmresWork<float> gm32;
   cudaStream_t hs = nullptr;
   cudaEvent_t ev = nullptr;
-  // graphs of one outer step: FP64, mixed, mixed with the learned smoother
-  cudaGraphExec_t graph[3] = {nullptr, nullptr, nullptr};
-  int64_t graph_kernels[3] = {0, 0, 0};
-  int32_t graph_inner[3] = {0, 0, 0};
+  // outer residual of this solve's steps in FP32 pairs (until a check in FP64
+  // disagrees with the convergence test, see solve_ws)
+  bool pair = false;
+  // graphs of one outer step: FP64, mixed, mixed with the learned smoother;
+  // + 3 for the same with the outer residual in FP32 pairs
+  cudaGraphExec_t graph[6] = {nullptr, nullptr, nullptr, nullptr, nullptr, nullptr};
+  int64_t graph_kernels[6] = {0, 0, 0, 0, 0, 0};
+  int32_t graph_inner[6] = {0, 0, 0, 0, 0, 0};
   double* pinned = nullptr;
   template <typename T>
   cpm::Work<T>& work(int l);
@@ -246,11 +263,15 @@ struct cpm_hier_s {
   std::vector<HLevel> L;
   DBuf<double> Ainv;     // coarse_mode 0: FP64 inverse
   DBuf<float> Ainv32;    // coarse_mode 1: FP32 inverse
+  DBuf<float> Ainv_f32;  // coarse_mode 0: the FP64 inverse rounded to FP32, for FP32
+                         // V-cycles (FP32 GEMV at twice the bandwidth and off the FP64
+                         // pipe); built when it takes at most kCoarseF32CopyMax points
   int32_t nc = 0;
   int32_t coarse_mode = 0;    // 0: FP64 inverse, 1: FP32 inverse (+FP64 refinement), 2: sweeps,
                               // 3: GMRES
   int32_t coarse_sweeps = 0;
   int32_t coarse_restarts = 3;
+  bool pair_resid = false;    // outer residual in FP32 pairs (k_extend_pair + k_resid_pair)
   cpm_mlp mlp = nullptr;
   std::unique_ptr<cpm::MlpLevelData> mlpd;
   bool learned_active = false;
@@ -280,7 +301,14 @@ static void alloc_workspace(const cpm_hier_s& H, Workspace& W, double* norms_slo
   W.f_own.alloc(nB0);
   W.r64.alloc(nB0);
   W.d64.alloc(nB0);
-  W.refv.alloc(H.L[0].lev->nplus());
+  if (H.pair_resid) {
+    W.dpair.alloc(H.L[0].lev->nplus());
+    W.rpair.alloc(H.L[0].lev->nplus());
+    W.dmax.alloc(kPairSlots);
+    CPM_CUDA_TRY(cudaMemset(W.dmax.get(), 0, sizeof(uint32_t) * kPairSlots));
+  } else {
+    W.refv.alloc(H.L[0].lev->nplus());
+  }
   W.r32.alloc(nB0);
   W.d32.alloc(nB0);
   if (H.coarse_mode == 3) {
@@ -382,6 +410,12 @@ static void coarse_solve(cpm_hier_s* H, Workspace* const* W, int G, const T* con
                          cudaStream_t st) {
   const int l = (int)H->L.size() - 1;
   if (H->coarse_mode == 0) {
+    if constexpr (sizeof(T) == 4) {
+      if (H->Ainv_f32.n > 0) {
+        launch_coarse_gemv32<T>(H->Ainv_f32.get(), f, u, G, H->nc, false, st);
+        return;
+      }
+    }
     launch_coarse_gemv<T>(H->Ainv.get(), f, u, G, H->nc, st);
     return;
   }
@@ -497,16 +531,23 @@ static void fmg(cpm_hier_s* H, Workspace& W, const T* f, T* u, cudaStream_t st) 
   }
 }
 
-// FP64 outer residual r = f - A u on the finest level with norms into W.norms,
-// in the relative form (differences formed from exact inputs; its rounding
-// floor is far below that of w = E u followed by the stencil at fine dx).
+// Outer residual r = f - A u on the finest level with norms into W.norms, in
+// the relative form (differences formed from exact inputs; its rounding floor
+// is far below that of w = E u followed by the stencil at fine dx), evaluated
+// in FP32 pairs on the FP32 pipe (default) or in FP64.
 static void outer_residual(cpm_hier_s* H, Workspace& W, const double* f, const double* u, double* r,
-                           cudaStream_t st) {
+                           cudaStream_t st, bool pair) {
   HLevel& lv = H->L[0];
   const LevelView<double> v = lv.view<double>();
   if (H->opts.op_form != CPM_OP_MBR) {  // direct form of Eq. 3.3
     level_op<double>(H, W, 0, LAP_RESID, f, u, r, W.part.get(), st);
     launch_norm_final(W.part.get(), paper_blocks(v), W.norms, st);
+    return;
+  }
+  if (pair && H->pair_resid) {
+    launch_extend_pair(v, u, W.dpair.get(), W.rpair.get(), W.dmax.get(), st);
+    launch_resid_pair(v, u, W.dpair.get(), W.rpair.get(), f, lv.c64.get(), H->c, r, W.part.get(), st);
+    launch_norm_final(W.part.get(), resid_pair_blocks(v), W.norms, st, W.dmax.get());
     return;
   }
   launch_extend_rel(v, u, W.w64[0].w.get(), W.refv.get(), st);
@@ -550,7 +591,7 @@ static void outer_step(cpm_hier_s* H, Workspace* const* W, int G, int mode, int 
     for (int g = 0; g < G; ++g) launch_axpy_scaled(W[g]->u_own.get(), W[g]->d32.get(), W[g]->norms, nB, st);
   }
   for (int g = 0; g < G; ++g)
-    outer_residual(H, *W[g], W[g]->f_own.get(), W[g]->u_own.get(), W[g]->r64.get(), st);
+    outer_residual(H, *W[g], W[g]->f_own.get(), W[g]->u_own.get(), W[g]->r64.get(), st, W[g]->pair);
 }
 
 static void outer_step(cpm_hier_s* H, Workspace& W, int mode, int inner, cudaStream_t st,
@@ -751,6 +792,7 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
   CPM_CHECK(o.relative == 0 || (o.relative == 1 && o.op_form == CPM_OP_MBR), CPM_ERR_ARG,
             "relative = 1 is for the CPM_OP_MBR operator");
   CPM_CHECK(o.ext_variant >= 0 && o.ext_variant <= 3, CPM_ERR_ARG, "ext_variant must be 0 .. 3");
+  CPM_CHECK(o.outer_f64 == 0 || o.outer_f64 == 1, CPM_ERR_ARG, "outer_f64 must be 0 or 1");
   CPM_CHECK(o.op_form == CPM_OP_MBR || o.smoother != CPM_SMOOTH_RM, CPM_ERR_ARG,
             "the paper-form operator is smoothed on A (Jacobi or red-black Gauss-Seidel)");
   if (!(o.c > 0)) o.c = 1.0;
@@ -771,6 +813,8 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
   H->L.emplace_back();
   H->L[0].lev.reset(new Level);
   copy_level(f0, *H->L[0].lev, st);
+  H->pair_resid = o.op_form == CPM_OP_MBR && o.outer_f64 == 0;
+  if (H->pair_resid) build_pair_weights(*H->L[0].lev, st);
   double dx = f0.dx;
   for (;;) {
     const double next = 2.0 * dx;
@@ -896,6 +940,11 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
                                 H->Ainv.get(), st);
     CPM_CUDA_TRY(cudaGetLastError());
     invert_dense(H->Ainv.get(), H->nc, st, err.get());
+    if (H->nc <= kCoarseF32CopyMax) {
+      H->Ainv_f32.alloc(nn);
+      k_round_f32<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(H->Ainv.get(), H->Ainv_f32.get(), (int64_t)nn);
+      CPM_CUDA_TRY(cudaGetLastError());
+    }
   } else if (H->coarse_mode == 1) {
     DBuf<float> A32(nn);
     CPM_CUDA_TRY(cudaMemsetAsync(A32.get(), 0, sizeof(float) * nn, st));
@@ -1025,7 +1074,7 @@ cpm_status cpm_vcycle(cpm_hier h, int32_t prec, const void* f, void* u, cpm_stre
 cpm_status cpm_residual(cpm_hier h, const double* f, const double* u, double* r, cpm_stream stream) {
   CPM_API_BEGIN
   CPM_CHECK(h != nullptr && u != nullptr && f != nullptr && r != nullptr, CPM_ERR_ARG, "NULL argument");
-  outer_residual(h, h->ws, f, u, r, (cudaStream_t)stream);
+  outer_residual(h, h->ws, f, u, r, (cudaStream_t)stream, h->pair_resid);
   CPM_CUDA_TRY(cudaGetLastError());
   CPM_API_END
 }
@@ -1039,7 +1088,7 @@ cpm_status cpm_residual_norms(cpm_hier h, const double* f, const double* u, doub
   Workspace& W = h->ws;
   launch_norm_partials<double>(f, nB, W.part.get(), st);
   launch_norm_final(W.part.get(), kNormBlocks, W.normf.get(), st);
-  outer_residual(h, W, f, u, W.r64.get(), st);
+  outer_residual(h, W, f, u, W.r64.get(), st, h->pair_resid);
   double hn[3], hf[3];
   CPM_CUDA_TRY(cudaMemcpyAsync(hn, W.norms, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CPM_CUDA_TRY(cudaMemcpyAsync(hf, W.normf.get(), 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -1059,6 +1108,27 @@ cpm_status cpm_residual_norms_noalloc(cpm_hier h, const double* f, const double*
   const HLevel& lv = h->L[0];
   residual_norms_noalloc(lv.view<double>(), f, u, lv.c64.get(), h->c, norms, (cudaStream_t)stream);
   CPM_API_END
+}
+
+// Size of the rounding error of an outer residual in FP32 pairs, from the
+// largest staged difference dmax = max |u - ref| (norms[3]): each extended
+// value carries about 2^-48 dmax, and the stencil adds 2d + 1 of them with
+// weights of total size (2d + 2d) / dx^2 + gamma = 6d / dx^2.  Measured errors
+// are about 0.4 of 2^-48 dmax 6d / dx^2 (unit circle and sphere, dx = 1/32 ..
+// 1/256, emulated; the GPU agrees at dx = 1/256); the estimate takes four times
+// 2^-48 dmax 6d / dx^2, about ten times the error.
+static double pair_error_estimate(const cpm_hier_s* h, double dmax) {
+  const Level& l0 = *h->L[0].lev;
+  return 4.0 * std::ldexp(dmax, -48) * 6.0 * l0.dim / (l0.dx * l0.dx);
+}
+
+// Whether an outer residual in FP32 pairs (relative size rel, the previous
+// one prev, estimated rounding error est) is checked in FP64 on the same
+// iterate: when it meets the tolerance only within the estimate, when it has
+// reached the estimate, or when it has stopped falling (at most halved).
+static bool pair_needs_check(double rel, double prev, double est, double tol, int it) {
+  if (rel <= tol) return rel + est > tol;
+  return rel <= est || (it > 0 && rel > 0.5 * prev);
 }
 
 // Options with defaults filled in and checked.
@@ -1123,6 +1193,7 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
   CPM_CUDA_TRY(cudaEventRecord(W.ev, us));
   CPM_CUDA_TRY(cudaStreamWaitEvent(st, W.ev, 0));
   CPM_CUDA_TRY(cudaMemcpyAsync(W.f_own.get(), f, nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  W.pair = h->pair_resid;
   if (o.zero_init)
     CPM_CUDA_TRY(cudaMemsetAsync(W.u_own.get(), 0, nB * sizeof(double), st));
   else
@@ -1133,11 +1204,11 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
   if (o.zero_init) {  // u = 0: the residual is f itself, and so are its norms
     CPM_CUDA_TRY(cudaMemcpyAsync(W.r64.get(), W.f_own.get(), nB * sizeof(double),
                                  cudaMemcpyDeviceToDevice, st));
-    CPM_CUDA_TRY(cudaMemcpyAsync(W.norms, W.normf.get(), 3 * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    CPM_CUDA_TRY(cudaMemcpyAsync(W.norms, W.normf.get(), 4 * sizeof(double), cudaMemcpyDeviceToDevice, st));
   } else {
-    outer_residual(h, W, W.f_own.get(), W.u_own.get(), W.r64.get(), st);
+    outer_residual(h, W, W.f_own.get(), W.u_own.get(), W.r64.get(), st, W.pair);
   }
-  CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.norms, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.norms, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
   const double fmax = W.pinned[4];
   CPM_CHECK(std::isfinite(fmax), CPM_ERR_ARG, "f is not finite");
@@ -1147,7 +1218,7 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
   h->learned_active = false;
   int gi = o.mode;
   cpm_solve_report rep{};
-  double rel = W.pinned[0] / fn, best = rel;
+  double rel = W.pinned[0] / fn, best = rel, prev = rel;
   cpm_status result = CPM_ERR_NOT_CONVERGED;
   int it = 0;
   // learned smoothing: iteration 0 runs plain Jacobi V-cycles and sets the
@@ -1157,6 +1228,17 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
   bool learned_on = false;
   double ref_factor = 0.0, learned_log = 0.0;
   for (;; ++it) {
+    if (W.pair) {
+      rep.pair_floor = pair_error_estimate(h, W.pinned[3]) / fn;
+      if (pair_needs_check(rel, prev, rep.pair_floor, o.tol, it)) {
+        outer_residual(h, W, W.f_own.get(), W.u_own.get(), W.r64.get(), st, false);
+        CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.norms, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        CPM_CUDA_TRY(cudaStreamSynchronize(st));
+        rel = W.pinned[0] / fn;
+        ++rep.f64_checks;
+        if (!(rel <= o.tol)) W.pair = false;
+      }
+    }
     if (it < CPM_MAX_HISTORY) rep.history[it] = rel;
     if (rel <= o.tol) { result = CPM_OK; break; }
     if (!std::isfinite(rel) || rel > 1e3 * best) { result = CPM_ERR_DIVERGED; break; }
@@ -1164,7 +1246,7 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
     best = std::min(best, rel);
     if (o.learned && it == 1 && !rep.fallback) learned_on = true;
     h->learned_active = learned_on;
-    gi = learned_on ? 2 : o.mode;
+    gi = (learned_on ? 2 : o.mode) + (W.pair ? 3 : 0);
     if (o.fmg && it == 0) {
       outer_step(h, W, o.mode, o.inner_cycles, st, true);
     } else if (o.use_graph) {
@@ -1174,9 +1256,9 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
     } else {
       outer_step(h, W, o.mode, o.inner_cycles, st);
     }
-    CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.norms, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.norms, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     CPM_CUDA_TRY(cudaStreamSynchronize(st));
-    const double prev = rel;
+    prev = rel;
     rel = W.pinned[0] / fn;
     if (o.learned) {
       const double fac = prev > 0 ? rel / prev : 0.0;
@@ -1279,9 +1361,11 @@ cpm_status cpm_mlp_destroy(cpm_mlp m) {
 cpm_status cpm_hier_set_smoother(cpm_hier h, cpm_mlp m) {
   CPM_API_BEGIN
   CPM_CHECK(h != nullptr, CPM_ERR_ARG, "hierarchy is NULL");
-  if (h->ws.graph[2]) {
-    cudaGraphExecDestroy(h->ws.graph[2]);
-    h->ws.graph[2] = nullptr;
+  for (int g : {2, 5}) {  // the graphs with the learned smoother
+    if (h->ws.graph[g]) {
+      cudaGraphExecDestroy(h->ws.graph[g]);
+      h->ws.graph[g] = nullptr;
+    }
   }
   h->mlp = m;
   if (m && !h->mlpd) {
@@ -1510,6 +1594,8 @@ struct cpm_batch_s {
   cudaGraphExec_t graph = nullptr;
   int graph_k = 0, graph_mode = -1, graph_inner = -1;
   std::vector<int> graph_sys;    // systems in the current graph
+  int64_t pair_epoch = 0;        // bumped when a system's outer residual leaves FP32 pairs
+  int64_t graph_epoch = -1;      // pair_epoch when the graph was captured
   int64_t graph_kernels = 0;
   int32_t chosen = 0;
   double tune_ms[8] = {0};
@@ -1585,7 +1671,8 @@ static int count_groups(const cpm_batch_s& b, const std::vector<int>& sys) {
 // kMaxGroup, one coarse-inverse pass for all of them); groups go to branches
 // largest first, each to the branch with the least work so far.
 static void capture_batch(cpm_batch_s& b, const std::vector<int>& sys, int K, int mode, int inner) {
-  if (b.graph && b.graph_k == K && b.graph_mode == mode && b.graph_inner == inner && b.graph_sys == sys)
+  if (b.graph && b.graph_k == K && b.graph_mode == mode && b.graph_inner == inner && b.graph_sys == sys &&
+      b.graph_epoch == b.pair_epoch)
     return;
   if (b.graph) {
     cudaGraphExecDestroy(b.graph);
@@ -1640,6 +1727,7 @@ static void capture_batch(cpm_batch_s& b, const std::vector<int>& sys, int K, in
   CPM_CUDA_TRY(cudaGraphInstantiate(&b.graph, g, 0));
   CPM_CUDA_TRY(cudaGraphDestroy(g));
   b.graph_k = K;
+  b.graph_epoch = b.pair_epoch;
   b.graph_mode = mode;
   b.graph_inner = inner;
   b.graph_sys = sys;
@@ -1708,6 +1796,8 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
     cudaStream_t st = b->fs[s % kMaxBranches];
     const int64_t nB = b->H[s]->L[0].lev->nB;
     CPM_CUDA_TRY(cudaMemcpyAsync(W.f_own.get(), f[s], nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (W.pair != b->H[s]->pair_resid) ++b->pair_epoch;
+    W.pair = b->H[s]->pair_resid;
     if (o.zero_init)
       CPM_CUDA_TRY(cudaMemsetAsync(W.u_own.get(), 0, nB * sizeof(double), st));
     else
@@ -1717,10 +1807,10 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
     if (o.zero_init) {  // u = 0: the residual is f itself, and so are its norms
       CPM_CUDA_TRY(cudaMemcpyAsync(W.r64.get(), W.f_own.get(), nB * sizeof(double),
                                    cudaMemcpyDeviceToDevice, st));
-      CPM_CUDA_TRY(cudaMemcpyAsync(W.norms, fn_all.get() + 4 * (size_t)s, 3 * sizeof(double),
+      CPM_CUDA_TRY(cudaMemcpyAsync(W.norms, fn_all.get() + 4 * (size_t)s, 4 * sizeof(double),
                                    cudaMemcpyDeviceToDevice, st));
     } else {
-      outer_residual(b->H[s], W, W.f_own.get(), W.u_own.get(), W.r64.get(), st);
+      outer_residual(b->H[s], W, W.f_own.get(), W.u_own.get(), W.r64.get(), st, W.pair);
     }
   }
   for (int k = 0; k < kMaxBranches; ++k) {
@@ -1734,12 +1824,12 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
                                cudaMemcpyDeviceToHost, b->ms));
   CPM_CUDA_TRY(cudaStreamSynchronize(b->ms));
   std::vector<cpm_solve_report> rep(ns);
-  std::vector<double> fmax(ns), rel(ns), best(ns);
+  std::vector<double> fmax(ns), rel(ns), best(ns), prev(ns);
   std::vector<int> done(ns, 0);
   for (int s = 0; s < ns; ++s) {
     CPM_CHECK(std::isfinite(hf[4 * (size_t)s]), CPM_ERR_ARG, "f is not finite");
     fmax[s] = hf[4 * (size_t)s] > 0 ? hf[4 * (size_t)s] : 1.0;
-    rel[s] = best[s] = b->host_norms[4 * (size_t)s] / fmax[s];
+    rel[s] = best[s] = prev[s] = b->host_norms[4 * (size_t)s] / fmax[s];
   }
   // autotuner: the first outer iterations try K = 1, 2, 4, ... concurrent
   // branches (each a real iteration of every active system)
@@ -1754,7 +1844,34 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
   cpm_status result = CPM_OK;
   std::vector<int> active, in_graph;
   int it = 0;
+  std::vector<int> check;
   for (;; ++it) {
+    // FP64 check of residuals in FP32 pairs that meet the tolerance or have
+    // stopped falling (as in cpm_solve); a system whose check misses the
+    // tolerance continues with FP64 residuals
+    check.clear();
+    for (int s = 0; s < ns; ++s) {
+      if (done[s] || !b->W[s]->pair) continue;
+      rep[s].pair_floor = pair_error_estimate(b->H[s], b->host_norms[4 * (size_t)s + 3]) / fmax[s];
+      if (pair_needs_check(rel[s], prev[s], rep[s].pair_floor, o.tol, it)) check.push_back(s);
+    }
+    if (!check.empty()) {
+      for (int s : check) {
+        Workspace& W = *b->W[s];
+        outer_residual(b->H[s], W, W.f_own.get(), W.u_own.get(), W.r64.get(), b->ms, false);
+      }
+      CPM_CUDA_TRY(cudaMemcpyAsync(b->host_norms, b->norms_all.get(), 4 * sizeof(double) * ns,
+                                   cudaMemcpyDeviceToHost, b->ms));
+      CPM_CUDA_TRY(cudaStreamSynchronize(b->ms));
+      for (int s : check) {
+        rel[s] = b->host_norms[4 * (size_t)s] / fmax[s];
+        ++rep[s].f64_checks;
+        if (!(rel[s] <= o.tol)) {
+          b->W[s]->pair = false;
+          ++b->pair_epoch;
+        }
+      }
+    }
     bool diverged = false;
     active.clear();
     for (int s = 0; s < ns; ++s) {
@@ -1802,7 +1919,10 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
         cache_store(*b, best_k);
       }
     }
-    for (int s : in_graph) rel[s] = b->host_norms[4 * (size_t)s] / fmax[s];
+    for (int s : in_graph) {
+      prev[s] = rel[s];
+      rel[s] = b->host_norms[4 * (size_t)s] / fmax[s];
+    }
   }
   if (result != CPM_OK)
     for (int s = 0; s < ns; ++s)

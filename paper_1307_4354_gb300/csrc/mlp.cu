@@ -13,8 +13,10 @@
 // of a residual field r is ||r - A du||^2 / ||r||^2; its gradient with
 // respect to du is -2 A^T (r - A du) / ||r||^2 (A^T through a transposed
 // neighbour gather and a transposed extension scatter over the extension
-// tiles), back-propagated through the network in FP32, reduced per CTA and
-// summed in a fixed order; Adam on FP32 master weights.
+// tiles), back-propagated through the network on the tensor cores (the three
+// contractions as BF16 mma.sync with FP32 accumulation, bias gradients in
+// FP32), reduced per CTA and summed in a fixed order; Adam on FP32 master
+// weights.
 #include <cuda_bf16.h>
 
 #include <cmath>
@@ -238,81 +240,176 @@ __global__ void __launch_bounds__(kFwdWarps * 32) k_mlp_forward(MlpFwdArgs A) {
 }
 
 // ----------------------------------------------------------------- backward
-// A fixed grid of CTAs; each loops over groups of kBwdPts points: dz2 = dy w3
-// [h2 > 0], dz1 = (dz2 W2^T) [h1 > 0], and every thread accumulates the
-// gradient entries it owns (parameter q = threadIdx.x + k * kBwdThreads) over
-// all of the CTA's groups in registers.  Each CTA writes one partial gradient
-// (part[blockIdx.x][kNParams]), summed in a fixed order by k_grad_reduce, so
-// the partials take kBwdCtas x 25 KB whatever the band size.
-constexpr int kBwdPts = 32;
-constexpr int kBwdThreads = 256;
+// The backward pass runs on a fixed grid of kBwdCtas CTAs, each writing one
+// partial gradient (kBwdCtas x 25 KB whatever the band size).
 constexpr int kBwdCtas = 2 * 152;
-constexpr int kBwdPer = (kNParams + kBwdThreads - 1) / kBwdThreads;  // 25 entries per thread
 
-__global__ void __launch_bounds__(kBwdThreads) k_mlp_backward(const float* params, const float* dy,
-                                                              const __nv_bfloat16* Xs,
-                                                              const __nv_bfloat16* H1,
-                                                              const __nv_bfloat16* H2, int32_t nB,
-                                                              float* part) {
-  __shared__ float x[kBwdPts][33], h1[kBwdPts][65], h2[kBwdPts][65], dz2[kBwdPts][65],
-      dz1[kBwdPts][65];
-  __shared__ float dys[kBwdPts];
-  float acc[kBwdPer];
+// Tensor-core backward.  A CTA of 4 warps loops over groups of 16 points;
+// per group the three contractions run as BF16 mma.sync.m16n8k16 with FP32
+// accumulation:
+//   dz1 = (dz2 W2^T) [h1 > 0]    M = 16 points, N = 64, K = 64  (warp w: dz1 columns 16w..16w+15)
+//   dW2 += H1^T dz2              M = 64, N = 64, K = 16 points (warp w: rows 16w..16w+15)
+//   dW1 += X^T dz1               M = 32, N = 64, K = 16 points (warp w: columns 16w..16w+15)
+// with dz2 = dy w3 [h2 > 0].  The operands sit in shared memory transposed so
+// that the K index (the points) is contiguous; the dW accumulators stay in
+// registers across all the CTA's groups; bias gradients are FP32 sums by 65
+// threads.  Each CTA writes one partial gradient, summed by k_grad_reduce.
+constexpr int kTcWarps = 4;
+constexpr int kTcS = 24;   // row stride (bf16) of the transposed 16-point tiles
+constexpr int kTcW2 = 72;  // row stride (bf16) of W2 in shared memory
+
+__global__ void __launch_bounds__(kTcWarps * 32) k_mlp_backward_tc(const float* params, const float* dy,
+                                                                   const __nv_bfloat16* Xs,
+                                                                   const __nv_bfloat16* H1,
+                                                                   const __nv_bfloat16* H2, int32_t nB,
+                                                                   float* part) {
+  __shared__ __align__(16) __nv_bfloat16 w2s[64 * kTcW2];   // w2s[k][j] = W2[k][j]
+  __shared__ __align__(16) __nv_bfloat16 xT[32 * kTcS];     // xT[f][p]
+  __shared__ __align__(16) __nv_bfloat16 h1T[64 * kTcS];    // h1T[k][p]
+  __shared__ __align__(16) __nv_bfloat16 dz2T[64 * kTcS];   // dz2T[j][p]
+  __shared__ __align__(16) __nv_bfloat16 dz1T[64 * kTcS];   // dz1T[k][p]
+  __shared__ __align__(16) __nv_bfloat16 dz2r[16 * kTcW2];  // dz2r[p][j] (A operand of dz1)
+  __shared__ float h1f[16][65], h2f[16][65], dz1f[16][65], w3s[64], dys[16];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int g = lane >> 2, t = lane & 3;
+  for (int q = tid; q < 64 * 64; q += blockDim.x)
+    w2s[(q >> 6) * kTcW2 + (q & 63)] = __float2bfloat16_rn(params[kOffW2 + q]);
+  for (int q = tid; q < 64; q += blockDim.x) w3s[q] = params[kOffW3 + q];
+  float acc2[8][4], acc1[2][2][4];  // dW2 rows 16w.., dW1 (m-tile, n-tile of the warp)
 #pragma unroll
-  for (int e = 0; e < kBwdPer; ++e) acc[e] = 0.f;
-  const int64_t ngroups = ((int64_t)nB + kBwdPts - 1) / kBwdPts;
+  for (int a = 0; a < 8; ++a)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) acc2[a][e] = 0.f;
+#pragma unroll
+  for (int a = 0; a < 2; ++a)
+#pragma unroll
+    for (int b = 0; b < 2; ++b)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc1[a][b][e] = 0.f;
+  float sb1 = 0.f, sb2 = 0.f, sw3 = 0.f, sb3 = 0.f;  // bias sums of threads 0..64
+  const int64_t ngroups = ((int64_t)nB + 15) / 16;
+  __syncthreads();
   for (int64_t grp = blockIdx.x; grp < ngroups; grp += gridDim.x) {
-    const int64_t p0 = grp * kBwdPts;
-    for (int q = threadIdx.x; q < kBwdPts * 64; q += blockDim.x) {
+    const int64_t p0 = grp * 16;
+    // operands of this group
+    for (int q = tid; q < 16 * 64; q += blockDim.x) {
       const int p = q >> 6, j = q & 63;
       const int64_t gp = p0 + p;
       const bool ok = gp < nB;
-      const float dyv = ok ? dy[gp] : 0.f;
+      const float h1v = ok ? __bfloat162float(H1[gp * 64 + j]) : 0.f;
       const float h2v = ok ? __bfloat162float(H2[gp * 64 + j]) : 0.f;
-      h1[p][j] = ok ? __bfloat162float(H1[gp * 64 + j]) : 0.f;
-      h2[p][j] = h2v;
-      dz2[p][j] = h2v > 0.f ? dyv * params[kOffW3 + j] : 0.f;
-      if (j < 32) x[p][j] = ok ? __bfloat162float(Xs[gp * 32 + j]) : 0.f;
+      const float dyv = ok ? dy[gp] : 0.f;
+      const float d2 = h2v > 0.f ? dyv * w3s[j] : 0.f;
+      h1f[p][j] = h1v;
+      h2f[p][j] = h2v;
+      h1T[j * kTcS + p] = __float2bfloat16_rn(h1v);
+      dz2T[j * kTcS + p] = __float2bfloat16_rn(d2);
+      dz2r[p * kTcW2 + j] = __float2bfloat16_rn(d2);
+      if (j < 32) xT[j * kTcS + p] = ok ? Xs[gp * 32 + j] : __float2bfloat16_rn(0.f);
       if (j == 0) dys[p] = dyv;
     }
     __syncthreads();
-    // dz1 = (dz2 W2^T) * [h1 > 0]
-    for (int q = threadIdx.x; q < kBwdPts * 64; q += blockDim.x) {
-      const int p = q >> 6, k = q & 63;
-      float s = 0.f;
-      if (h1[p][k] > 0.f)
-        for (int j = 0; j < 64; ++j) s += dz2[p][j] * params[kOffW2 + k * 64 + j];
-      dz1[p][k] = s;
+    // dz1 columns 16 warp .. 16 warp + 15: A = dz2 (points x j), B[j][k] = W2[k][j]
+    {
+      float c[2][4];
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+        for (int e = 0; e < 4; ++e) c[nt][e] = 0.f;
+#pragma unroll
+      for (int kc = 0; kc < 4; ++kc) {
+        uint32_t a[4];
+        a[0] = *reinterpret_cast<const uint32_t*>(&dz2r[g * kTcW2 + kc * 16 + 2 * t]);
+        a[1] = *reinterpret_cast<const uint32_t*>(&dz2r[(g + 8) * kTcW2 + kc * 16 + 2 * t]);
+        a[2] = *reinterpret_cast<const uint32_t*>(&dz2r[g * kTcW2 + kc * 16 + 8 + 2 * t]);
+        a[3] = *reinterpret_cast<const uint32_t*>(&dz2r[(g + 8) * kTcW2 + kc * 16 + 8 + 2 * t]);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int n = 16 * warp + 8 * nt + g;
+          const __nv_bfloat16* wb = &w2s[n * kTcW2 + kc * 16 + 2 * t];
+          mma_bf16(c[nt], a, *reinterpret_cast<const uint32_t*>(wb),
+                   *reinterpret_cast<const uint32_t*>(wb + 8));
+        }
+      }
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int k0 = 16 * warp + 8 * nt + 2 * t;
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const int p = g + (e >> 1) * 8, k = k0 + (e & 1);
+          const float v = h1f[p][k] > 0.f ? c[nt][e] : 0.f;
+          dz1f[p][k] = v;
+          dz1T[k * kTcS + p] = __float2bfloat16_rn(v);
+        }
+      }
     }
     __syncthreads();
+    // dW2 rows 16 warp ..: A[k][p] = h1T, B[p][j] = dz2T (as [j][p])
+    {
+      uint32_t a[4];
+      const int m0 = 16 * warp;
+      a[0] = *reinterpret_cast<const uint32_t*>(&h1T[(m0 + g) * kTcS + 2 * t]);
+      a[1] = *reinterpret_cast<const uint32_t*>(&h1T[(m0 + g + 8) * kTcS + 2 * t]);
+      a[2] = *reinterpret_cast<const uint32_t*>(&h1T[(m0 + g) * kTcS + 8 + 2 * t]);
+      a[3] = *reinterpret_cast<const uint32_t*>(&h1T[(m0 + g + 8) * kTcS + 8 + 2 * t]);
 #pragma unroll
-    for (int e = 0; e < kBwdPer; ++e) {
-      const int q = threadIdx.x + e * kBwdThreads;
-      float s = 0.f;
-      if (q < kOffB1) {  // dW1[f][k] = sum_p x[p][f] dz1[p][k] (row 31: the zero feature)
-        const int f = q >> 6, k = q & 63;
-        for (int p = 0; p < kBwdPts; ++p) s += x[p][f] * dz1[p][k];
-      } else if (q < kOffW2) {  // db1
-        for (int p = 0; p < kBwdPts; ++p) s += dz1[p][q - kOffB1];
-      } else if (q < kOffB2) {  // dW2[k][j] = sum_p h1[p][k] dz2[p][j]
-        const int k = (q - kOffW2) >> 6, j = (q - kOffW2) & 63;
-        for (int p = 0; p < kBwdPts; ++p) s += h1[p][k] * dz2[p][j];
-      } else if (q < kOffW3) {  // db2
-        for (int p = 0; p < kBwdPts; ++p) s += dz2[p][q - kOffB2];
-      } else if (q < kOffB3) {  // dw3[j] = sum_p dy[p] relu(z2)[p][j]
-        for (int p = 0; p < kBwdPts; ++p) s += dys[p] * h2[p][q - kOffW3];
-      } else if (q == kOffB3) {
-        for (int p = 0; p < kBwdPts; ++p) s += dys[p];
+      for (int nt = 0; nt < 8; ++nt) {
+        const __nv_bfloat16* bb = &dz2T[(nt * 8 + g) * kTcS + 2 * t];
+        mma_bf16(acc2[nt], a, *reinterpret_cast<const uint32_t*>(bb),
+                 *reinterpret_cast<const uint32_t*>(bb + 8));
       }
-      acc[e] += s;
+    }
+    // dW1 columns 16 warp ..: A[f][p] = xT, B[p][k] = dz1T (as [k][p])
+#pragma unroll
+    for (int mt = 0; mt < 2; ++mt) {
+      uint32_t a[4];
+      a[0] = *reinterpret_cast<const uint32_t*>(&xT[(16 * mt + g) * kTcS + 2 * t]);
+      a[1] = *reinterpret_cast<const uint32_t*>(&xT[(16 * mt + g + 8) * kTcS + 2 * t]);
+      a[2] = *reinterpret_cast<const uint32_t*>(&xT[(16 * mt + g) * kTcS + 8 + 2 * t]);
+      a[3] = *reinterpret_cast<const uint32_t*>(&xT[(16 * mt + g + 8) * kTcS + 8 + 2 * t]);
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const __nv_bfloat16* bb = &dz1T[(16 * warp + 8 * nt + g) * kTcS + 2 * t];
+        mma_bf16(acc1[mt][nt], a, *reinterpret_cast<const uint32_t*>(bb),
+                 *reinterpret_cast<const uint32_t*>(bb + 8));
+      }
+    }
+    // bias gradients (FP32)
+    if (tid < 64) {
+      for (int p = 0; p < 16; ++p) {
+        sb1 += dz1f[p][tid];
+        const float d2 = h2f[p][tid] > 0.f ? dys[p] * w3s[tid] : 0.f;
+        sb2 += d2;
+        sw3 += dys[p] * h2f[p][tid];
+      }
+    } else if (tid == 64) {
+      for (int p = 0; p < 16; ++p) sb3 += dys[p];
     }
     __syncthreads();
   }
   float* out = part + (int64_t)blockIdx.x * kNParams;
 #pragma unroll
-  for (int e = 0; e < kBwdPer; ++e) {
-    const int q = threadIdx.x + e * kBwdThreads;
-    if (q < kNParams) out[q] = acc[e];
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int k = 16 * warp + g + (e >> 1) * 8, j = nt * 8 + 2 * t + (e & 1);
+      out[kOffW2 + k * 64 + j] = acc2[nt][e];
+    }
+#pragma unroll
+  for (int mt = 0; mt < 2; ++mt)
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int f = 16 * mt + g + (e >> 1) * 8, k = 16 * warp + 8 * nt + 2 * t + (e & 1);
+        out[kOffW1 + f * 64 + k] = acc1[mt][nt][e];
+      }
+  if (tid < 64) {
+    out[kOffB1 + tid] = sb1;
+    out[kOffB2 + tid] = sb2;
+    out[kOffW3 + tid] = sw3;
+  } else if (tid == 64) {
+    out[kOffB3] = sb3;
   }
 }
 
@@ -532,8 +629,8 @@ void mlp_loss_grad(const float* params, const MlpLevelData& D, const LevelView<f
   k_extend_transpose<<<L.ntiles, 64, 0, st>>>(L, tb.t.get(), tb.et.get());
   k_mlp_dy<<<nb256, 256, 0, st>>>(tb.z.get(), tb.et.get(), cvec, cval, L.gamma, L.inv_h2, tb.S.get(),
                                    dx2, tb.loss.get() + 1, nB, tb.dy.get());
-  k_mlp_backward<<<tb.nparts, kBwdThreads, 0, st>>>(params, tb.dy.get(), tb.Xs.get(), tb.H1.get(),
-                                                    tb.H2.get(), nB, tb.part.get());
+  k_mlp_backward_tc<<<tb.nparts, kTcWarps * 32, 0, st>>>(params, tb.dy.get(), tb.Xs.get(), tb.H1.get(),
+                                                         tb.H2.get(), nB, tb.part.get());
   k_grad_reduce<<<nblk(kNParams, 256), 256, 0, st>>>(tb.part.get(), tb.nparts, tb.grad.get());
   count_launch(9);
   CPM_CUDA_TRY(cudaGetLastError());

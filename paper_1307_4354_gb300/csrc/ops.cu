@@ -7,6 +7,7 @@
 
 #include "ops.cuh"
 #include "gemv.cuh"
+#include "pair.cuh"
 
 #include <atomic>
 
@@ -350,6 +351,116 @@ void launch_resid_rel(const LevelView<double>& L, const double* u, const double*
                          part, refv, st);
 }
 
+// ---------------------------------------------------- outer residual, FP32 pairs
+// r = f - c u + M u on B from the pair extension (delta_j pairs, ref_j floats):
+// M u_i = S / dx^2 + gamma ((ref_i - u_i) + delta_i) with
+// S = sum over the 2d neighbours k of (ref_k - ref_i) + (delta_k - delta_i),
+// summed in pairs (the reference differences are exact TwoSums of floats),
+// scaled by 1/dx^2 and gamma as pairs.  FP64 work per point: ref_i - u_i,
+// f - c u_i and the sum with M u_i, and r^2 for the norm (the maximum is taken
+// on the bit patterns of |r|).  Each thread takes kPairPts points (strided by
+// the block), so the block's norm reduction is shared by several points.
+constexpr int kPairPts = 4;
+
+// Largest |x| and sum of x^2 over the block into part[2 b], part[2 b + 1];
+// m holds the bit pattern of a non-negative double (ordered as an integer).
+__device__ inline void block_maxbits_sum(unsigned long long m, double s, double* part) {
+  __shared__ unsigned long long sm[32];
+  __shared__ double ss[32];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    s += __shfl_xor_sync(0xffffffffu, s, o);
+  }
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) { sm[wid] = m; ss[wid] = s; }
+  __syncthreads();
+  if (wid == 0) {
+    const int nw = (blockDim.x + 31) >> 5;
+    m = lane < nw ? sm[lane] : 0ull;
+    s = lane < nw ? ss[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+      s += __shfl_xor_sync(0xffffffffu, s, o);
+    }
+    if (lane == 0) {
+      part[2 * blockIdx.x] = __longlong_as_double((long long)m);
+      part[2 * blockIdx.x + 1] = s;
+    }
+  }
+}
+
+template <int DIM>
+__global__ void __launch_bounds__(256) k_resid_pair(LevelView<double> L, const double* __restrict__ u,
+                                                    const float2* __restrict__ dp,
+                                                    const float* __restrict__ rp,
+                                                    const double* __restrict__ f,
+                                                    const double* __restrict__ cvec, double cval,
+                                                    float2 ih2, float2 gam, double* __restrict__ r,
+                                                    double* part) {
+  unsigned long long rm = 0ull;
+  double rs = 0.0;
+#pragma unroll
+  for (int j = 0; j < kPairPts; ++j) {
+    const int32_t i = (blockIdx.x * kPairPts + j) * blockDim.x + threadIdx.x;
+    if (i >= L.nB) break;
+    int32_t k[2 * DIM];
+#pragma unroll
+    for (int q = 0; q < 2 * DIM; ++q) k[q] = __ldg(L.nbr + (int64_t)q * L.nB + i);
+    const float ri = __ldg(rp + i);
+    const float2 di = __ldg(dp + i);
+    float sh = 0.f, sl = 0.f;
+#pragma unroll
+    for (int q = 0; q < 2 * DIM; ++q) {
+      const float rk = __ldg(rp + k[q]);
+      const float2 dk = __ldg(dp + k[q]);
+      float ah, al, bh, bl, ch, cl, t;
+      two_sum(rk, -ri, ah, al);
+      two_sum(dk.x, -di.x, bh, bl);
+      two_sum(ah, bh, ch, cl);
+      two_sum(sh, ch, sh, t);
+      sl = __fadd_rn(sl, __fadd_rn(__fadd_rn(al, bl), __fadd_rn(cl, t)));
+      sl = __fadd_rn(sl, __fsub_rn(dk.y, di.y));
+    }
+    float Sh, Sl, lh, ll;
+    fast_two_sum(sh, sl, Sh, Sl);
+    pair_mul(Sh, Sl, ih2.x, ih2.y, lh, ll);             // S / dx^2
+    const double ui = u[i];
+    const float2 e = pair_split(pair_f2d(ri) - ui);      // ref_i - u_i
+    float th, tl, gh, gl, mh, ml;
+    pair_add(e.x, e.y, di.x, di.y, th, tl);
+    pair_mul(th, tl, gam.x, gam.y, gh, gl);             // gamma ((ref_i - u_i) + delta_i)
+    pair_add(lh, ll, gh, gl, mh, ml);                   // M u_i
+    const double c = cvec ? cvec[i] : cval;
+    const double res = (f[i] - c * ui) + pair_to_f64(mh, ml);
+    r[i] = res;
+    rm = max(rm, (unsigned long long)__double_as_longlong(fabs(res)));
+    rs += res * res;
+  }
+  if (part) block_maxbits_sum(rm, rs, part);
+}
+
+int resid_pair_blocks(const LevelView<double>& L) {
+  return (int)((L.nB + 256 * kPairPts - 1) / (256 * kPairPts));
+}
+
+void launch_resid_pair(const LevelView<double>& L, const double* u, const float2* delta,
+                       const float* refv, const double* f, const double* cvec, double cval, double* r,
+                       double* part, cudaStream_t st) {
+  if (L.nB <= 0) return;
+  const unsigned nb = (unsigned)resid_pair_blocks(L);
+  const double ih2 = (double)L.inv_h2, gam = (double)L.gamma;
+  const float ih2h = (float)ih2, gamh = (float)gam;
+  const float2 ih2p = make_float2(ih2h, (float)(ih2 - (double)ih2h));
+  const float2 gamp = make_float2(gamh, (float)(gam - (double)gamh));
+  if (L.dim == 3)
+    k_resid_pair<3><<<nb, 256, 0, st>>>(L, u, delta, refv, f, cvec, cval, ih2p, gamp, r, part);
+  else
+    k_resid_pair<2><<<nb, 256, 0, st>>>(L, u, delta, refv, f, cvec, cval, ih2p, gamp, r, part);
+  count_launch();
+}
+
 // ----------------------------------------------------------------- Ruuth-Merriman
 template <typename T>
 void launch_rm_jacobi(const LevelView<T>& L, const T* u, const T* f, const T* cvec, T cval, T omega,
@@ -564,8 +675,19 @@ void launch_norm_partials(const T* x, int64_t n, double* part, cudaStream_t st) 
   count_launch();
 }
 
-// out[0] = max|x|, out[1] = sum x^2, out[2] = 1 / max|x| (0 if max is 0).
-__global__ void k_norm_final(const double* part, int nblocks, double* out) {
+// out[0] = max|x|, out[1] = sum x^2, out[2] = 1 / max|x| (0 if max is 0);
+// out[3] = the largest of the kPairSlots float slots of dmax (non-negative,
+// compared as integers), which are reset to 0, or 0 without dmax.
+__global__ void k_norm_final(const double* part, int nblocks, double* out, uint32_t* dmax) {
+  __shared__ uint32_t dm;
+  if (threadIdx.x == 0) dm = 0u;
+  __syncthreads();
+  if (dmax) {
+    for (int i = threadIdx.x; i < kPairSlots; i += blockDim.x) {
+      atomicMax(&dm, dmax[i]);
+      dmax[i] = 0u;
+    }
+  }
   double m = 0.0, s = 0.0;
   for (int i = threadIdx.x; i < nblocks; i += blockDim.x) {
     m = fmax(m, part[2 * i]);
@@ -585,11 +707,12 @@ __global__ void k_norm_final(const double* part, int nblocks, double* out) {
     out[0] = M;
     out[1] = S;
     out[2] = M > 0.0 ? 1.0 / M : 0.0;
+    out[3] = (double)__uint_as_float(dm);
   }
 }
 
-void launch_norm_final(const double* part, int nblocks, double* out, cudaStream_t st) {
-  k_norm_final<<<1, 1024, 0, st>>>(part, nblocks, out);
+void launch_norm_final(const double* part, int nblocks, double* out, cudaStream_t st, uint32_t* dmax) {
+  k_norm_final<<<1, 1024, 0, st>>>(part, nblocks, out, dmax);
   count_launch();
 }
 

@@ -27,6 +27,7 @@ struct LevelView {
   const uint32_t* erec;
   const float* efr;     // E-order FP32 fractions
   const double* ew64;   // E-order FP64 weights
+  const float2* ewp;    // E-order weights as FP32 pairs (finest level, pair residual)
   int32_t ntiles;
   int ext_variant;            // FP32 extension work decomposition (ExtVariant)
   const uint32_t* echunk;     // chunk records (ext.cu)
@@ -99,6 +100,21 @@ void launch_lap(const LevelView<T>& L, LapMode mode, const T* u, const T* w, con
 // Number of blocks (2 partial doubles each) of a RESID / RESID_REL stencil pass.
 int lap_blocks_f64(const LevelView<double>& L);
 
+// The outer residual in FP32-pair arithmetic (relative form, see k_extend_pair
+// and k_resid_pair): launch_extend_pair fills delta (pairs) and refv (floats)
+// over B+ (needs L.ewp), launch_resid_pair forms r = f - c u + M u on B with
+// norm partials of resid_pair_blocks(L) blocks into part.
+// kPairSlots slots collect the largest |u - ref| staged by any tile (as float
+// bits, one atomic max per tile into slot tile mod kPairSlots), which bounds
+// the size of the rounding errors of the pair arithmetic.
+constexpr int kPairSlots = 1024;
+void launch_extend_pair(const LevelView<double>& L, const double* u, float2* delta, float* refv,
+                        uint32_t* dmax, cudaStream_t st);
+void launch_resid_pair(const LevelView<double>& L, const double* u, const float2* delta,
+                       const float* refv, const double* f, const double* cvec, double cval, double* r,
+                       double* part, cudaStream_t st);
+int resid_pair_blocks(const LevelView<double>& L);
+
 // The paper's scheme M_p u = E_1 (L_B u) - gamma (u - E_3 u) (Eq. 3.3):
 // v = L_B u on B (band-restricted Laplacian); then, with w = E_3 u on B,
 //   APPLY : out = M_p u
@@ -143,7 +159,10 @@ void launch_transfer(const TransferView<T>& tv, const T* src, T* dst, bool add, 
 constexpr int kNormBlocks = 1216;  // 152 SMs x 8
 template <typename T>
 void launch_norm_partials(const T* x, int64_t n, double* part, cudaStream_t st);
-void launch_norm_final(const double* part, int nblocks, double* out, cudaStream_t st);
+// out[0..3] = max, sum of squares, 1/max of the partials' vector, and the
+// largest value in dmax's kPairSlots slots (0 without dmax; the slots are reset).
+void launch_norm_final(const double* part, int nblocks, double* out, cudaStream_t st,
+                       uint32_t* dmax = nullptr);
 
 // Mixed precision helpers.
 void launch_scale_to_f32(const double* r, const double* norms, float* r32, int64_t n, cudaStream_t st);

@@ -89,7 +89,8 @@ class Hierarchy:
                  coarse_sweeps: int = 0, coarse_f64_max: int = 0, coarse_dense_max: int = 0,
                  op_form: str = "mbr", transfer_deg: int = 1, cycle: int = 1,
                  a_device: torch.Tensor | None = None, relative: bool = False,
-                 ext_variant: int | None = None, coarse_gmres: int = 0, stream=None):
+                 ext_variant: int | None = None, coarse_gmres: int = 0, outer_f64: bool = False,
+                 stream=None):
         o = capi.cpm_mg_opts()
         o.coarsest_dx, o.nu1, o.nu2, o.omega = coarsest_dx, nu1, nu2, omega
         o.smoother, o.transfer_deg, o.c = _SMOOTHERS[smoother], transfer_deg, c
@@ -103,6 +104,7 @@ class Hierarchy:
         o.relative = int(relative)
         o.ext_variant = 0 if ext_variant is None else int(ext_variant) + 1
         o.coarse_gmres = coarse_gmres
+        o.outer_f64 = int(outer_f64)
         o.c_device = _ptr(c_device, torch.float64, band.nb) if c_device is not None else None
         self.band = band
         self.handle = capi.cpm_build_hierarchy(band.handle, o, _stream(stream))
@@ -201,7 +203,8 @@ class Hierarchy:
                    "rel_residual": rep.rel_residual, "history": list(rep.history[:n]),
                    "seconds": rep.seconds, "learned_iters": rep.learned_iters,
                    "fallback": bool(rep.fallback), "jacobi_factor": rep.jacobi_factor,
-                   "learned_factor": rep.learned_factor, "learned_worst": rep.learned_worst}
+                   "learned_factor": rep.learned_factor, "learned_worst": rep.learned_worst,
+                   "f64_checks": rep.f64_checks, "pair_floor": rep.pair_floor}
 
     def residual_norms(self, f: torch.Tensor, u: torch.Tensor, stream=None):
         return capi.cpm_residual_norms(self.handle, _ptr(f, torch.float64, self.nb),
@@ -223,7 +226,7 @@ def _report(st, rep) -> dict:
     n = min(rep.iters + 1, capi.CPM_MAX_HISTORY)
     return {"status": st, "iters": rep.iters, "converged": bool(rep.converged),
             "rel_residual": rep.rel_residual, "history": list(rep.history[:n]),
-            "seconds": rep.seconds}
+            "seconds": rep.seconds, "f64_checks": rep.f64_checks, "pair_floor": rep.pair_floor}
 
 
 class Batch:

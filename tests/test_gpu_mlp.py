@@ -101,7 +101,11 @@ def test_train_scales_fields_and_matches_train_steps():
         r = fields[k // 3]
         H.smoother_train_step((r / r.abs().max()).float().contiguous(), 1e-3, want_loss=False)
     pa, pb = a.get_params(), b.get_params()
-    assert np.abs(pa - pb).max() <= 1e-6 * np.abs(pb).max()
+    # The loss gradient's transposed extension accumulates with atomics, so the
+    # two runs agree to FP32 rounding only, and Adam's normalised step m/sqrt(v)
+    # magnifies that where a gradient component is near zero; a wrong scaling
+    # or schedule moves parameters by a whole step (lr = 1e-3).
+    assert np.abs(pa - pb).max() <= 1e-5 * np.abs(pb).max()
     with pytest.raises(pkg.capi.CpmError):
         a.train([(H, torch.zeros_like(fields[0]))], steps=1)
 

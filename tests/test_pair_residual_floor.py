@@ -1,0 +1,137 @@
+"""Rounding floor of the outer residual in FP32-pair arithmetic (CPU emulation
+of the GPU's evaluation, see pair_arith.py) on the unit sphere down to
+dx = 1/512.
+
+The outer residual r = f - A u of the defect correction must resolve a relative
+residual of 1e-10 (Sec. 4.3's stopping test).  Its relative form (reference
+values, differences delta_j = sum_m E_jm (u_m - ref_j)) evaluated in FP32 pairs
+keeps about 2^-48 of each difference, and the stencil divides those errors by
+dx^2: since the differences shrink like dx, the floor grows like 1/dx.  Here it is measured on a patch of band nodes
+(every node's 2d neighbours and their cubic stencils; u = the harmonic
+extension u(cp(x)) of a smooth solution) against the same formula in extended
+precision with each stencil's weights normalised to sum 1, and must stay at or
+below 1e-11 of max |M u| at dx = 1/512.  The FP64 relative form is measured
+beside it for scale.
+"""
+import numpy as np
+import pytest
+
+import pair_arith as pa
+from oracle import geometry
+from oracle.interp import lagrange_1d
+import synth
+
+LO = -2.0
+
+
+def _patch(dx, n, seed):
+    """n band nodes near the unit sphere and their 6 grid neighbours."""
+    rng = np.random.default_rng(seed)
+    y = rng.standard_normal((n, 3))
+    y /= np.linalg.norm(y, axis=1, keepdims=True)
+    y *= 1.0 + rng.uniform(-2.0, 2.0, (n, 1)) * dx  # within two cells of S
+    ijk = np.round((y - LO) / dx).astype(np.int64)
+    offs = np.array([[-1, 0, 0], [1, 0, 0], [0, -1, 0], [0, 1, 0], [0, 0, -1], [0, 0, 1]])
+    nodes = np.concatenate([ijk[:, None, :], ijk[:, None, :] + offs[None]], axis=1)  # (n, 7, 3)
+    return nodes
+
+
+def _stencils(nodes, dx, ufun):
+    """Per node: 1-D weights (FP64), stencil values u (n, 4, 4, 4) [z][y][x]
+    and the reference value.  The GPU takes one reference per extension tile
+    (the points whose stencil bases lie in one 4^3 brick): u at the last band
+    node of that brick, rounded to float32; modelled here by the brick's node
+    (3, 3, 3)."""
+    X = LO + nodes * dx
+    cp, _ = geometry.closest_point(geometry.sphere(1.0), X)
+    t = (cp - LO) / dx
+    fl = np.floor(t)
+    s = t - fl
+    base = fl.astype(np.int64) - 1
+    W = [lagrange_1d(s[:, a], 3) for a in range(3)]
+    o = np.arange(4)
+    grid = base[:, None, None, None, :] + np.stack(np.meshgrid(o, o, o, indexing="ij"), axis=-1)[None][..., ::-1]
+    Xg = LO + grid.reshape(-1, 3) * dx
+    cpg, _ = geometry.closest_point(geometry.sphere(1.0), Xg)
+    vals = ufun(cpg).reshape(grid.shape[:-1])  # [n][z][y][x]
+    rnode = (base // 4) * 4 + 3
+    rcp, _ = geometry.closest_point(geometry.sphere(1.0), LO + rnode * dx)
+    ref = ufun(rcp).astype(np.float32)
+    return W, vals, ref, ufun(cp)
+
+
+def _floors(dx, n=1500, seed=0):
+    def ufun(p):
+        return synth.sphere_harmonics(p)[0]
+    nodes = _patch(dx, n, seed)
+    N = nodes.shape[0]
+    flat = nodes.reshape(-1, 3)
+    W, vals, ref, _ = _stencils(flat, dx, ufun)
+    u_node = ufun(geometry.closest_point(geometry.sphere(1.0), LO + flat * dx)[0])
+    h2 = dx * dx
+    gamma = 6.0 / h2
+    c = 1.0
+    # extended precision: weights normalised to sum 1
+    ld = np.longdouble
+    Wt = (W[2].astype(ld)[:, :, None, None] * W[1].astype(ld)[:, None, :, None]
+          * W[0].astype(ld)[:, None, None, :])
+    Wt /= Wt.sum(axis=(1, 2, 3), keepdims=True)
+    w_ex = (Wt * vals.astype(ld)).sum(axis=(1, 2, 3)).reshape(N, 7)
+    ui = u_node.reshape(N, 7)[:, 0]
+    Mu_ex = (w_ex[:, 1:] - w_ex[:, :1]).sum(axis=1) / ld(h2) + ld(gamma) * (w_ex[:, 0] - ui.astype(ld))
+    f = np.asarray(c * ui - Mu_ex, dtype=np.float64)  # r = 0 in extended precision (to its rounding)
+    r_ex = (f.astype(ld) - ld(c) * ui.astype(ld)) + Mu_ex
+    scale = float(np.abs(Mu_ex).max())
+    # FP64 relative form
+    refd = ref.astype(np.float64)
+    d64 = vals - refd[:, None, None, None]
+    delta64 = np.einsum("nzyx,nx,ny,nz->n", d64, W[0], W[1], W[2]).reshape(N, 7)
+    refN = refd.reshape(N, 7)
+    s = ((refN[:, 1:] - refN[:, :1]) + (delta64[:, 1:] - delta64[:, :1])).sum(axis=1)
+    r64 = (f - c * ui) + (s / h2 + gamma * ((refN[:, 0] - ui) + delta64[:, 0]))
+    # FP32-pair relative form
+    dh, dl = pa.split64(d64)
+    w = [pa.split64(W[a]) for a in range(3)]
+    ph, pl = pa.extension_delta(w[0], w[1], w[2], dh, dl)
+    ph, pl = ph.reshape(N, 7), pl.reshape(N, 7)
+    refN32 = ref.reshape(N, 7)
+    rp = pa.residual(ui, f, c, refN32[:, 0], ph[:, 0], pl[:, 0], refN32[:, 1:], ph[:, 1:], pl[:, 1:],
+                     1.0 / h2, gamma)
+    e64 = float(np.abs(r64 - r_ex).max()) / scale
+    ep = float(np.abs(rp - r_ex).max()) / scale
+    return e64, ep
+
+
+@pytest.mark.skipif(np.finfo(np.longdouble).eps >= np.finfo(np.float64).eps,
+                    reason="no extended precision on this platform")
+def test_pair_floor_sphere_to_dx_512():
+    res = {dx: _floors(dx) for dx in (1 / 128, 1 / 256, 1 / 512)}
+    for dx, (e64, ep) in res.items():
+        assert e64 < 2e-13, (dx, e64)
+        assert ep <= 1e-11, (dx, ep, e64)
+    # the pair floor grows like 1/dx, not 1/dx^2 (differences shrink with dx)
+    assert res[1 / 512][1] < 4.0 * res[1 / 128][1] + 1e-13, res
+
+
+def test_pair_emulation_primitives():
+    """TwoSum and the exact product split are error-free, the split of a
+    float64 keeps 48 bits or more, and a pair contraction of the partition of
+    unity reproduces a constant to the pair precision."""
+    rng = np.random.default_rng(1)
+    a = rng.standard_normal(1000).astype(np.float32)
+    b = (rng.standard_normal(1000) * 1e-3).astype(np.float32)
+    s, e = pa.two_sum(a, b)
+    assert np.all(s.astype(np.float64) + e.astype(np.float64) == a.astype(np.float64) + b.astype(np.float64))
+    p, q = pa.mul_first(a, np.zeros_like(a), b, np.zeros_like(b))
+    assert np.all(p.astype(np.float64) + q.astype(np.float64) == a.astype(np.float64) * b.astype(np.float64))
+    d = rng.standard_normal(1000) * 10.0 ** rng.uniform(-20, 20, 1000)
+    h, l = pa.split64(d)
+    assert np.all(np.abs(pa.to64(h, l) - d) <= np.abs(d) * 2.0 ** -48)
+    assert np.all(np.abs(h.astype(np.float64) - d) <= np.abs(d) * 2.0 ** -24)
+    assert np.all(np.abs(l) <= np.abs(h) * 2.0 ** -24)
+    s = rng.uniform(0, 1, (200, 3))
+    W = [pa.split64(lagrange_1d(s[:, k], 3)) for k in range(3)]
+    one = np.ones((200, 4, 4, 4))
+    oh, ol = pa.split64(one * (1 / 3))
+    h, l = pa.extension_delta(W[0], W[1], W[2], oh, ol)
+    assert np.abs(pa.to64(h, l) - 1 / 3).max() < 1e-14
