@@ -675,10 +675,9 @@ __device__ __forceinline__ void contract_pair(const PairBox<DIM>& sm, int o, con
 }
 
 template <int DIM>
-#ifndef CPM_PAIR_MINB
-#define CPM_PAIR_MINB 16  // resident CTAs per SM asked of the register allocator
-#endif
-__global__ void __launch_bounds__(kExtThreads, CPM_PAIR_MINB) k_extend_pair(LevelView<double> L, const double* __restrict__ u,
+// (72 registers, 14 CTAs per SM; asking for 16 CTAs gave 64 registers with a
+// small spill and no gain: 396 us against 389 us at dx = 1/256)
+__global__ void __launch_bounds__(kExtThreads) k_extend_pair(LevelView<double> L, const double* __restrict__ u,
                                                              float2* __restrict__ delta,
                                                              float* __restrict__ refv, uint32_t* dmax) {
   __shared__ PairBox<DIM> sm;

@@ -301,13 +301,12 @@ static void alloc_workspace(const cpm_hier_s& H, Workspace& W, double* norms_slo
   W.f_own.alloc(nB0);
   W.r64.alloc(nB0);
   W.d64.alloc(nB0);
+  W.refv.alloc(H.L[0].lev->nplus());  // FP64 form (also the check of the pair form)
   if (H.pair_resid) {
     W.dpair.alloc(H.L[0].lev->nplus());
     W.rpair.alloc(H.L[0].lev->nplus());
     W.dmax.alloc(kPairSlots);
     CPM_CUDA_TRY(cudaMemset(W.dmax.get(), 0, sizeof(uint32_t) * kPairSlots));
-  } else {
-    W.refv.alloc(H.L[0].lev->nplus());
   }
   W.r32.alloc(nB0);
   W.d32.alloc(nB0);

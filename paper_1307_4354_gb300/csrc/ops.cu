@@ -435,7 +435,7 @@ __global__ void __launch_bounds__(256) k_resid_pair(LevelView<double> L, const d
     const double c = cvec ? cvec[i] : cval;
     const double res = (f[i] - c * ui) + pair_to_f64(mh, ml);
     r[i] = res;
-    rm = max(rm, (unsigned long long)__double_as_longlong(fabs(res)));
+    rm = max(rm, (unsigned long long)__double_as_longlong(res) & 0x7FFFFFFFFFFFFFFFull);  // |res|
     rs += res * res;
   }
   if (part) block_maxbits_sum(rm, rs, part);

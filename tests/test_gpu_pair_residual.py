@@ -87,7 +87,10 @@ def test_pair_residual_fullsize_solve(dx):
     r64 = H64.residual(f, u)
     fmax = float(f.abs().max())
     rel64 = float(r64.abs().max()) / fmax  # the solve's test: max |r| / max |f|
-    assert rel64 <= 1e-10 and abs(rel64 - rep["rel_residual"]) <= 1e-3 * rel64, (rel64, rep)
+    # the reported residual is the FP64 one after a check, else the pair one,
+    # which is within the solve's estimate of the FP64 one
+    assert rel64 <= 1e-10, (rel64, rep)
+    assert abs(rel64 - rep["rel_residual"]) <= max(rep["pair_floor"], 1e-3 * rel64), (rel64, rep)
     H64.close()
     Hp = pkg.Hierarchy(g, coarsest_dx=1 / 8, residual="plain", nu1=4, nu2=4)
     rp = Hp.residual(f, u)
@@ -101,17 +104,19 @@ def test_pair_residual_fullsize_solve(dx):
 
 @pytest.mark.parametrize("mode", ["f64", "mixed"])
 def test_tolerance_below_the_pair_floor(mode):
-    """Circle dx = 1/256, tol = 2e-12, below the pair floor (about 7e-12 here):
-    the solve notices that the pair residual stops falling, checks in FP64,
-    finishes with FP64 residuals, and the result meets the tolerance in FP64."""
+    """Circle dx = 1/64, tol = 1e-12: below the pair floor (about 1.3e-12 here)
+    but above what FP64 reaches (the sparse direct solution's residual is about
+    2e-12 in extended precision, the iteration gets below 1e-12).  The solve
+    notices that the pair residual cannot decide, checks in FP64, finishes with
+    FP64 residuals, and the result meets the tolerance in FP64."""
     torch, pkg = require_cuda()
-    g = pkg.Band("circle", (), 1 / 256)
+    g = pkg.Band("circle", (), 1 / 64)
     H = pkg.Hierarchy(g, coarsest_dx=1 / 8)
     H64 = pkg.Hierarchy(g, coarsest_dx=1 / 8, outer_f64=True)
     _, cp, _ = g.export()
     _, f_h = synth.circle_fourier(cp[: g.nb])
     f = torch.from_numpy(f_h).cuda()
-    u, rep = H.solve(f, tol=2e-12, max_iter=60, mode=mode, inner_cycles=2)
+    u, rep = H.solve(f, tol=1e-12, max_iter=80, mode=mode)
     assert rep["converged"] and rep["f64_checks"] >= 1, rep
     r64 = H64.residual(f, u)
-    assert float(r64.abs().max()) / float(f.abs().max()) <= 2e-12
+    assert float(r64.abs().max()) / float(f.abs().max()) <= 1e-12
