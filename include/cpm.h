@@ -445,12 +445,16 @@ typedef struct cpm_solve_report {
  * is FP64 in both modes; the outer residual is evaluated as cpm_residual
  * (FP32 pairs unless outer_f64).  With pairs, the residual also yields an
  * estimate of its rounding error (4 x 2^-48 max|u - u_ref| 6d / dx^2, about
- * ten times the measured error); a pair residual that meets the tolerance only
- * within that estimate, or has reached it, or has stopped falling (at most
- * halved by an outer iteration), is checked by the FP64 evaluation of the
- * same iterate, and if that check misses the tolerance the rest of the solve
- * uses FP64 residuals.  Synchronous (reads the residual norms once per outer
- * iteration).  report may be NULL.
+ * ten times the measured error).  A pair residual that meets the tolerance
+ * only within that estimate is checked pointwise: the points whose |r_i| lies
+ * within the estimate of the tolerance (at most 65536; more fall back to the
+ * next check) are evaluated in FP64, and the solve has converged if none
+ * exceeds the tolerance (rel_residual is then their largest |r_i|).  A pair
+ * residual that has reached its estimate, has stopped falling (at most halved
+ * by an outer iteration) or failed the pointwise check is replaced by the
+ * full FP64 evaluation of the same iterate, and if that misses the tolerance
+ * the rest of the solve uses FP64 residuals.  Synchronous (reads the
+ * residual norms once per outer iteration).  report may be NULL.
  * Errors: CPM_ERR_NOT_CONVERGED, CPM_ERR_DIVERGED (u holds the last iterate).
  */
 cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opts* opts,

@@ -77,6 +77,62 @@ __global__ void __launch_bounds__(kGemvWarps * 32) k_dense_gemv(const M* __restr
   }
 }
 
+// The same product for an FP32 matrix whose rows start on 16-byte boundaries
+// (leading dimension ld, a multiple of 4; columns n .. ld-1 are zero): each
+// lane streams groups of four columns with 16-byte loads, so that a warp has
+// four times the bytes in flight of the scalar form.  FP32 accumulation.
+template <typename T, bool ADD, int NV>
+__global__ void __launch_bounds__(kGemvWarps * 32) k_dense_gemv_v4(const float* __restrict__ A, int32_t ld,
+                                                                   GemvVectors<T> v, int32_t n) {
+  constexpr int kChunk = (4096 / NV) / 128 * 128;  // a multiple of 128 columns
+  __shared__ __align__(16) float sb[NV][kChunk];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t row0 = blockIdx.x * kGemvRowsPerBlock + warp * kGemvRowsPerWarp;
+  const float* a[kGemvRowsPerWarp];
+  bool ok[kGemvRowsPerWarp];
+  float acc[kGemvRowsPerWarp][NV];
+#pragma unroll
+  for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+    ok[r] = row0 + r < n;
+    a[r] = A + (size_t)(ok[r] ? row0 + r : 0) * ld;
+#pragma unroll
+    for (int q = 0; q < NV; ++q) acc[r][q] = 0.f;
+  }
+  for (int32_t c0 = 0; c0 < ld; c0 += kChunk) {
+    const int32_t cn = min(kChunk, ld - c0);
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      for (int32_t j = threadIdx.x; j < cn; j += blockDim.x)
+        sb[q][j] = c0 + j < n ? (float)v.b[q][c0 + j] : 0.f;
+    __syncthreads();
+#pragma unroll 2
+    for (int32_t j = 4 * lane; j < cn; j += 128) {
+      float4 bj[NV];
+#pragma unroll
+      for (int q = 0; q < NV; ++q) bj[q] = *reinterpret_cast<const float4*>(&sb[q][j]);
+#pragma unroll
+      for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+        if (!ok[r]) continue;
+        const float4 av = __ldg(reinterpret_cast<const float4*>(a[r] + c0 + j));
+#pragma unroll
+        for (int q = 0; q < NV; ++q)
+          acc[r][q] += av.x * bj[q].x + av.y * bj[q].y + av.z * bj[q].z + av.w * bj[q].w;
+      }
+    }
+  }
+#pragma unroll
+  for (int r = 0; r < kGemvRowsPerWarp; ++r) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      float s = acc[r][q];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+      if (lane == 0 && ok[r]) v.x[q][row0 + r] = ADD ? v.x[q][row0 + r] + (T)s : (T)s;
+    }
+  }
+}
+
 inline unsigned dense_gemv_blocks(int32_t n) {
   return (unsigned)((n + kGemvRowsPerBlock - 1) / kGemvRowsPerBlock);
 }
@@ -98,6 +154,27 @@ void launch_dense_gemv(const M* A, const T* const* b, T* const* x, int G, int32_
       case 2: k_dense_gemv<M, T, ADD, 2><<<grid, kGemvWarps * 32, 0, st>>>(A, v, n); break;
       case 3: k_dense_gemv<M, T, ADD, 3><<<grid, kGemvWarps * 32, 0, st>>>(A, v, n); break;
       default: k_dense_gemv<M, T, ADD, 4><<<grid, kGemvWarps * 32, 0, st>>>(A, v, n); break;
+    }
+  }
+}
+
+// x_g = A b_g for g < G with the row-aligned FP32 matrix of k_dense_gemv_v4.
+template <typename T>
+void launch_dense_gemv_v4(const float* A, int32_t ld, const T* const* b, T* const* x, int G, int32_t n,
+                          cudaStream_t st) {
+  for (int g0 = 0; g0 < G; g0 += kGemvMaxVectors) {
+    const int nv = G - g0 < kGemvMaxVectors ? G - g0 : kGemvMaxVectors;
+    GemvVectors<T> v{};
+    for (int q = 0; q < nv; ++q) {
+      v.b[q] = b[g0 + q];
+      v.x[q] = x[g0 + q];
+    }
+    const unsigned grid = dense_gemv_blocks(n);
+    switch (nv) {
+      case 1: k_dense_gemv_v4<T, false, 1><<<grid, kGemvWarps * 32, 0, st>>>(A, ld, v, n); break;
+      case 2: k_dense_gemv_v4<T, false, 2><<<grid, kGemvWarps * 32, 0, st>>>(A, ld, v, n); break;
+      case 3: k_dense_gemv_v4<T, false, 3><<<grid, kGemvWarps * 32, 0, st>>>(A, ld, v, n); break;
+      default: k_dense_gemv_v4<T, false, 4><<<grid, kGemvWarps * 32, 0, st>>>(A, ld, v, n); break;
     }
   }
 }

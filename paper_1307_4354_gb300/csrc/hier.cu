@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "gmres.cuh"
+#include "gemv.cuh"
 #include "mlp.cuh"
 
 namespace cpm {
@@ -64,13 +65,18 @@ __global__ void k_diag_A(const double* diagM, const double* cvec, double cval, d
 #define CPM_TRANSFER_INDEXED 1
 #endif
 
-// dst = src rounded to FP32.
-__global__ void k_round_f32(const double* src, float* dst, int64_t n) {
+// dst (n rows of ld floats) = src (n x n, row-major) rounded to FP32, the
+// padding columns n .. ld-1 zero.
+__global__ void k_round_f32(const double* src, int32_t n, int32_t ld, float* dst) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i < n) dst[i] = (float)src[i];
+  if (i >= (int64_t)n * ld) return;
+  const int64_t r = i / ld, c = i - r * ld;
+  dst[i] = c < n ? (float)src[r * n + c] : 0.f;
 }
 // Largest coarsest level whose FP64 inverse also gets an FP32 copy (256 MB).
 constexpr int32_t kCoarseF32CopyMax = 8192;
+// Most candidate points of a pointwise FP64 check of a pair residual.
+constexpr int32_t kCheckCap = 1 << 16;
 
 __global__ void k_transfer_index(const uint64_t* base, int32_t n, int dim, BrickView src, int32_t* idx) {
   const int32_t j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -226,6 +232,8 @@ struct Workspace {
   cpm::DBuf<float2> dpair;  // pair form: delta_j = (E u)_j - ref_j over the finest B+
   cpm::DBuf<float> rpair;   // pair form: ref_j
   cpm::DBuf<uint32_t> dmax; // pair form: slots of the largest staged |u - ref| (norms[3])
+  cpm::DBuf<int32_t> chk_list, chk_count;      // pointwise FP64 check: candidate points
+  cpm::DBuf<unsigned long long> chk_max;       // and the largest |r| among them (bits)
   cpm::DBuf<float> r32, d32;
   cpm::GmresWork<double> gm64;  // coarsest-level GMRES (coarse mode 3)
   cpm::GmresWork<float> gm32;
@@ -265,7 +273,9 @@ struct cpm_hier_s {
   DBuf<float> Ainv32;    // coarse_mode 1: FP32 inverse
   DBuf<float> Ainv_f32;  // coarse_mode 0: the FP64 inverse rounded to FP32, for FP32
                          // V-cycles (FP32 GEMV at twice the bandwidth and off the FP64
-                         // pipe); built when it takes at most kCoarseF32CopyMax points
+                         // pipe); built when it takes at most kCoarseF32CopyMax points;
+                         // rows padded with zeros to ld_f32 (a multiple of 4) columns
+  int32_t ld_f32 = 0;
   int32_t nc = 0;
   int32_t coarse_mode = 0;    // 0: FP64 inverse, 1: FP32 inverse (+FP64 refinement), 2: sweeps,
                               // 3: GMRES
@@ -307,6 +317,9 @@ static void alloc_workspace(const cpm_hier_s& H, Workspace& W, double* norms_slo
     W.rpair.alloc(H.L[0].lev->nplus());
     W.dmax.alloc(kPairSlots);
     CPM_CUDA_TRY(cudaMemset(W.dmax.get(), 0, sizeof(uint32_t) * kPairSlots));
+    W.chk_list.alloc(kCheckCap);
+    W.chk_count.alloc(1);
+    W.chk_max.alloc(1);
   }
   W.r32.alloc(nB0);
   W.d32.alloc(nB0);
@@ -411,7 +424,8 @@ static void coarse_solve(cpm_hier_s* H, Workspace* const* W, int G, const T* con
   if (H->coarse_mode == 0) {
     if constexpr (sizeof(T) == 4) {
       if (H->Ainv_f32.n > 0) {
-        launch_coarse_gemv32<T>(H->Ainv_f32.get(), f, u, G, H->nc, false, st);
+        launch_dense_gemv_v4<T>(H->Ainv_f32.get(), H->ld_f32, f, u, G, H->nc, st);
+        count_launch((G + kGemvMaxVectors - 1) / kGemvMaxVectors);
         return;
       }
     }
@@ -940,8 +954,11 @@ cpm_status cpm_build_hierarchy(cpm_band finest, const cpm_mg_opts* opts_in, cpm_
     CPM_CUDA_TRY(cudaGetLastError());
     invert_dense(H->Ainv.get(), H->nc, st, err.get());
     if (H->nc <= kCoarseF32CopyMax) {
-      H->Ainv_f32.alloc(nn);
-      k_round_f32<<<(unsigned)((nn + 255) / 256), 256, 0, st>>>(H->Ainv.get(), H->Ainv_f32.get(), (int64_t)nn);
+      H->ld_f32 = (H->nc + 3) / 4 * 4;
+      const int64_t np = (int64_t)H->nc * H->ld_f32;
+      H->Ainv_f32.alloc((size_t)np);
+      k_round_f32<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(H->Ainv.get(), H->nc, H->ld_f32,
+                                                               H->Ainv_f32.get());
       CPM_CUDA_TRY(cudaGetLastError());
     }
   } else if (H->coarse_mode == 1) {
@@ -1130,6 +1147,28 @@ static bool pair_needs_check(double rel, double prev, double est, double tol, in
   return rel <= est || (it > 0 && rel > 0.5 * prev);
 }
 
+// Pointwise FP64 check of the pair residual in W.r64 (iterate W.u_own): the
+// points with |r_i| > thr (absolute) evaluated in FP64.  Returns the largest
+// such |r_i|, or -1 if there were more than kCheckCap candidates.  Synchronous.
+static double pointwise_check(cpm_hier_s* h, Workspace& W, double thr, cudaStream_t st) {
+  const HLevel& lv = h->L[0];
+  launch_pointwise_check(lv.view<double>(), W.u_own.get(), W.f_own.get(), lv.c64.get(), h->c,
+                         W.r64.get(), thr, W.chk_list.get(), kCheckCap, W.chk_count.get(),
+                         W.chk_max.get(), st);
+  int32_t cnt = 0;
+  unsigned long long mb = 0;
+  CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned + 5, W.chk_count.get(), sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned + 6, W.chk_max.get(), sizeof(unsigned long long),
+                               cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaStreamSynchronize(st));
+  std::memcpy(&cnt, W.pinned + 5, sizeof(cnt));
+  std::memcpy(&mb, W.pinned + 6, sizeof(mb));
+  if (cnt > kCheckCap) return -1.0;
+  double m;
+  std::memcpy(&m, &mb, sizeof(m));
+  return m;
+}
+
 // Options with defaults filled in and checked.
 static cpm_solve_opts solve_opts(const cpm_solve_opts* opts_in) {
   cpm_solve_opts o{};
@@ -1230,12 +1269,19 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
     if (W.pair) {
       rep.pair_floor = pair_error_estimate(h, W.pinned[3]) / fn;
       if (pair_needs_check(rel, prev, rep.pair_floor, o.tol, it)) {
-        outer_residual(h, W, W.f_own.get(), W.u_own.get(), W.r64.get(), st, false);
-        CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.norms, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
-        CPM_CUDA_TRY(cudaStreamSynchronize(st));
-        rel = W.pinned[0] / fn;
         ++rep.f64_checks;
-        if (!(rel <= o.tol)) W.pair = false;
+        // meets the tolerance within the estimate: only the points whose pair
+        // residual lies within the estimate of the tolerance can violate it
+        const double m = rel <= o.tol ? pointwise_check(h, W, (o.tol - rep.pair_floor) * fn, st) : -1.0;
+        if (m >= 0.0 && m <= o.tol * fn) {
+          rel = m / fn;
+        } else {
+          outer_residual(h, W, W.f_own.get(), W.u_own.get(), W.r64.get(), st, false);
+          CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.norms, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+          CPM_CUDA_TRY(cudaStreamSynchronize(st));
+          rel = W.pinned[0] / fn;
+          if (!(rel <= o.tol)) W.pair = false;
+        }
       }
     }
     if (it < CPM_MAX_HISTORY) rep.history[it] = rel;
@@ -1259,7 +1305,10 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
     CPM_CUDA_TRY(cudaStreamSynchronize(st));
     prev = rel;
     rel = W.pinned[0] / fn;
-    if (o.learned) {
+    // a reduction factor is judged only where the residual is well above the
+    // pair rounding error (near it the factor says more about the rounding)
+    const bool judged = !W.pair || rel > 2.0 * pair_error_estimate(h, W.pinned[3]) / fn;
+    if (o.learned && judged) {
       const double fac = prev > 0 ? rel / prev : 0.0;
       if (it == 0) {
         ref_factor = fac;
@@ -1853,6 +1902,24 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
       if (done[s] || !b->W[s]->pair) continue;
       rep[s].pair_floor = pair_error_estimate(b->H[s], b->host_norms[4 * (size_t)s + 3]) / fmax[s];
       if (pair_needs_check(rel[s], prev[s], rep[s].pair_floor, o.tol, it)) check.push_back(s);
+    }
+    if (!check.empty()) {
+      // a residual that meets the tolerance within the estimate: pointwise
+      // check first (as in cpm_solve); the others get the full FP64 residual
+      std::vector<int> full;
+      for (int s : check) {
+        Workspace& W = *b->W[s];
+        if (rel[s] <= o.tol) {
+          const double m = pointwise_check(b->H[s], W, (o.tol - rep[s].pair_floor) * fmax[s], b->ms);
+          if (m >= 0.0 && m <= o.tol * fmax[s]) {
+            ++rep[s].f64_checks;
+            rel[s] = m / fmax[s];
+            continue;
+          }
+        }
+        full.push_back(s);
+      }
+      check.swap(full);
     }
     if (!check.empty()) {
       for (int s : check) {

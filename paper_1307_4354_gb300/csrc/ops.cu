@@ -4,6 +4,7 @@
 // restriction and prolongation (Sec. 4.3), norms, and the setup kernels for
 // diag(M) and the coarsest-level matrix.
 #include <cmath>
+#include <cstring>
 
 #include "ops.cuh"
 #include "gemv.cuh"
@@ -459,6 +460,107 @@ void launch_resid_pair(const LevelView<double>& L, const double* u, const float2
   else
     k_resid_pair<2><<<nb, 256, 0, st>>>(L, u, delta, refv, f, cvec, cval, ih2p, gamp, r, part);
   count_launch();
+}
+
+// ------------------------------------------------- pointwise FP64 residual check
+// After an outer residual in FP32 pairs that meets the tolerance only within
+// its error estimate, only the band points whose |r_i| exceeds thr = (tol -
+// estimate) max|f| can violate the tolerance.  k_check_select lists them (at
+// most cap; *count may exceed cap, the list is then incomplete) and
+// k_check_points evaluates r_i there in FP64, in the relative form with the
+// point's own value as the common reference: delta_j = sum_m E_jm (u_m - u_i)
+// for j = i and its 2d neighbours (cubic weights from the fractions, stencil
+// nodes through the brick tables), M u_i = sum_q (delta_kq - delta_i) / dx^2 +
+// gamma delta_i, r_i = f_i - c_i u_i + M u_i; the maximum |r_i| goes to *maxbits
+// (bit pattern of a non-negative double).  The stencil rows of one point are
+// summed with shared-memory atomics, so the last bits of r_i may vary from
+// run to run.
+__global__ void k_check_select(const double* __restrict__ r, int32_t nB, unsigned long long thr_bits,
+                               int32_t* __restrict__ list, int32_t cap, int32_t* count) {
+  const int32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= nB) return;
+  const unsigned long long a = (unsigned long long)__double_as_longlong(r[i]) & 0x7FFFFFFFFFFFFFFFull;
+  if (a > thr_bits) {
+    const int32_t p = atomicAdd(count, 1);
+    if (p < cap) list[p] = i;
+  }
+}
+
+// One warp per candidate point i: the 2d + 1 extension values it needs (at i
+// and at its Laplacian neighbours) are split into 4-node rows of their cubic
+// stencils, spread over the lanes, and summed per value in shared memory.
+constexpr int kCheckWarps = 4;
+
+template <int DIM>
+__global__ void __launch_bounds__(kCheckWarps * 32) k_check_points(
+    LevelView<double> L, const double* __restrict__ u, const double* __restrict__ f,
+    const double* __restrict__ cvec, double cval, const int32_t* __restrict__ list,
+    const int32_t* count, int32_t cap, unsigned long long* maxbits) {
+  constexpr int R = DIM == 3 ? 16 : 4;  // stencil rows of 4 nodes per value
+  constexpr int NJ = 2 * DIM + 1;       // values: the point, then its neighbours
+  __shared__ double part[kCheckWarps][NJ];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int32_t n = min(*count, cap);
+  for (int32_t t = blockIdx.x * kCheckWarps + warp; t < n; t += gridDim.x * kCheckWarps) {
+    const int32_t i = list[t];
+    const double ui = u[i];
+    if (lane < NJ) part[warp][lane] = 0.0;
+    __syncwarp();
+    for (int e = lane; e < NJ * R; e += 32) {
+      const int jj = e / R, row = e % R;
+      const int32_t j = jj == 0 ? i : __ldg(L.nbr + (int64_t)(jj - 1) * L.nB + i);
+      const uint64_t kk = __ldg(L.key + j);
+      const int bx = key_x(kk) + key_ox(kk), by = key_y(kk) + key_oy(kk);
+      const int bz = DIM == 3 ? key_z(kk) + key_oz(kk) : 0;
+      const int b = row & 3, c = row >> 2;
+      double w[3][4];  // cubic Lagrange weights at nodes -1, 0, 1, 2 per axis
+#pragma unroll
+      for (int a = 0; a < DIM; ++a) {
+        const double sf = __ldg(L.fr + a * L.nplus + j);
+        const double sm1 = sf - 1.0, sm2 = sf - 2.0, sp1 = sf + 1.0;
+        const double p = sf * sm1, q = sp1 * sm2;
+        w[a][0] = -(p * sm2) * (1.0 / 6.0);
+        w[a][1] = (q * sm1) * 0.5;
+        w[a][2] = -(q * sf) * 0.5;
+        w[a][3] = (p * sp1) * (1.0 / 6.0);
+      }
+      double acc = 0.0;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        const int32_t m = band_index(L.bv, bx + a, by + b, bz + c);
+        acc += w[0][a] * ((m >= 0 ? __ldg(u + m) : ui) - ui);
+      }
+      atomicAdd(&part[warp][jj], w[1][b] * (DIM == 3 ? w[2][c] : 1.0) * acc);
+    }
+    __syncwarp();
+    if (lane == 0) {
+      const double di = part[warp][0];
+      double s = 0.0;
+      for (int q = 1; q < NJ; ++q) s += part[warp][q] - di;
+      const double c = cvec ? cvec[i] : cval;
+      const double r = f[i] - c * ui + (s * L.inv_h2 + L.gamma * di);
+      atomicMax(maxbits, (unsigned long long)__double_as_longlong(r) & 0x7FFFFFFFFFFFFFFFull);
+    }
+    __syncwarp();
+  }
+}
+
+void launch_pointwise_check(const LevelView<double>& L, const double* u, const double* f,
+                            const double* cvec, double cval, const double* r, double thr,
+                            int32_t* list, int32_t cap, int32_t* count, unsigned long long* maxbits,
+                            cudaStream_t st) {
+  CPM_CUDA_TRY(cudaMemsetAsync(count, 0, sizeof(int32_t), st));
+  CPM_CUDA_TRY(cudaMemsetAsync(maxbits, 0, sizeof(unsigned long long), st));
+  if (L.nB <= 0) return;
+  unsigned long long thr_bits = 0ull;
+  if (thr > 0.0) std::memcpy(&thr_bits, &thr, sizeof(thr));
+  k_check_select<<<nblk(L.nB, 256), 256, 0, st>>>(r, L.nB, thr_bits, list, cap, count);
+  const unsigned grid = 2 * 152;  // warps loop over the candidates
+  if (L.dim == 3)
+    k_check_points<3><<<grid, kCheckWarps * 32, 0, st>>>(L, u, f, cvec, cval, list, count, cap, maxbits);
+  else
+    k_check_points<2><<<grid, kCheckWarps * 32, 0, st>>>(L, u, f, cvec, cval, list, count, cap, maxbits);
+  count_launch(2);
 }
 
 // ----------------------------------------------------------------- Ruuth-Merriman

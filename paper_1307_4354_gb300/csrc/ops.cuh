@@ -114,6 +114,14 @@ void launch_resid_pair(const LevelView<double>& L, const double* u, const float2
                        const float* refv, const double* f, const double* cvec, double cval, double* r,
                        double* part, cudaStream_t st);
 int resid_pair_blocks(const LevelView<double>& L);
+// Pointwise FP64 check of a pair residual r: lists the band points with
+// |r_i| > thr (at most cap; *count gets the number of candidates, which may
+// exceed cap) and sets *maxbits to the bit pattern of the largest |r_i| there,
+// evaluated in FP64 (see k_check_points).
+void launch_pointwise_check(const LevelView<double>& L, const double* u, const double* f,
+                            const double* cvec, double cval, const double* r, double thr,
+                            int32_t* list, int32_t cap, int32_t* count, unsigned long long* maxbits,
+                            cudaStream_t st);
 
 // The paper's scheme M_p u = E_1 (L_B u) - gamma (u - E_3 u) (Eq. 3.3):
 // v = L_B u on B (band-restricted Laplacian); then, with w = E_3 u on B,
