@@ -42,7 +42,7 @@ EXTEND32_BYTES_BPLUS = 20
 EXTEND32_BYTES_B = 4
 # DRAM bytes (read + write) of one FP32 extension launch over B+ of the unit
 # sphere at dx = 1/256, from one ncu capture of the same kernel and workload.
-EXTEND32_TRAFFIC = 165.8112e6 + 21.328128e6
+EXTEND32_TRAFFIC = 165.824768e6 + 21.474048e6
 
 
 def _sphere_rhs(y):

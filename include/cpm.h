@@ -528,9 +528,10 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
                            const cpm_solve_opts* opts, cpm_solve_report* reports, cpm_stream stream);
 
 /* Concurrency chosen by the autotuner (0 before the first solve) and the
- * measured device time of one outer iteration (ms) for each K tried
- * (tune_ms[q] for K = 2^q, q < 8; 0 where not tried).  Host outputs, either
- * may be NULL. */
+ * measured device time of one outer iteration (ms) for each K tried, scaled
+ * to the whole batch by the band points its graph covered (systems converge
+ * while the candidates are tried) (tune_ms[q] for K = 2^q, q < 8; 0 where not
+ * tried).  Host outputs, either may be NULL. */
 cpm_status cpm_batch_info(cpm_batch b, int32_t* concurrency, double* tune_ms);
 
 /* Free the workspaces and streams of the batch (not its hierarchies). */

@@ -79,8 +79,8 @@ __global__ void __launch_bounds__(kGemvWarps * 32) k_dense_gemv(const M* __restr
 
 // The same product for an FP32 matrix whose rows start on 16-byte boundaries
 // (leading dimension ld, a multiple of 4; columns n .. ld-1 are zero): each
-// lane streams groups of four columns with 16-byte loads, so that a warp has
-// four times the bytes in flight of the scalar form.  FP32 accumulation.
+// lane streams groups of four columns with 16-byte loads, four groups per row
+// in flight.  FP32 accumulation.
 template <typename T, bool ADD, int NV>
 __global__ void __launch_bounds__(kGemvWarps * 32) k_dense_gemv_v4(const float* __restrict__ A, int32_t ld,
                                                                    GemvVectors<T> v, int32_t n) {
@@ -106,7 +106,7 @@ __global__ void __launch_bounds__(kGemvWarps * 32) k_dense_gemv_v4(const float* 
       for (int32_t j = threadIdx.x; j < cn; j += blockDim.x)
         sb[q][j] = c0 + j < n ? (float)v.b[q][c0 + j] : 0.f;
     __syncthreads();
-#pragma unroll 2
+#pragma unroll 4
     for (int32_t j = 4 * lane; j < cn; j += 128) {
       float4 bj[NV];
 #pragma unroll

@@ -1974,12 +1974,18 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
                                  cudaMemcpyDeviceToHost, b->ms));
     CPM_CUDA_TRY(cudaStreamSynchronize(b->ms));
     if (ci < cand.size()) {
+      // systems converge during the tuning iterations, so each candidate's
+      // time is scaled to the whole batch by the band points its graph covered
       float ms = 0.f;
       CPM_CUDA_TRY(cudaEventElapsedTime(&ms, b->t0, b->t1));
+      double all = 0.0, covered = 0.0;
+      for (int s = 0; s < ns; ++s) all += (double)b->H[s]->L[0].lev->nB;
+      for (int s : in_graph) covered += (double)b->H[s]->L[0].lev->nB;
+      const double scaled = covered > 0.0 ? ms * all / covered : ms;
       int slot = 0;
       while ((1 << slot) < K && slot < 7) ++slot;
-      b->tune_ms[slot] = ms;
-      if (ms < best_ms) { best_ms = ms; best_k = K; }
+      b->tune_ms[slot] = scaled;
+      if (scaled < best_ms) { best_ms = scaled; best_k = K; }
       if (++ci == cand.size()) {
         b->chosen = best_k;
         cache_store(*b, best_k);
