@@ -715,47 +715,6 @@ __global__ void __launch_bounds__(kExtThreads) k_extend_pair(LevelView<double> L
   }
 }
 
-// FP32 extension by chunks: one CTA per tile, one thread per chunk (up to
-// kChunkMax points with one stencil base).  The thread loads the base's 4^d
-// values from the staged box into registers once (16 vector loads in 3-D) and
-// evaluates each point of the chunk from them, so the shared-memory traffic
-// per point drops by the chunk length (2.7 points per chunk on the sphere).
-template <int DIM>
-__device__ __forceinline__ float contract_regs(const float4 (&v)[DIM == 3 ? 16 : 4],
-                                               const PointWeights<float, DIM>& pw) {
-  float2 q01 = make_float2(0.f, 0.f), q23 = q01;
-#pragma unroll
-  for (int c = 0; c < (DIM == 3 ? 4 : 1); ++c) {
-    float2 p01, p23;
-#pragma unroll
-    for (int b = 0; b < 4; ++b) {
-      const float4 x = v[c * 4 + b];
-      const float2 wyb = make_float2(pw.wy[b], pw.wy[b]);
-      if (b == 0) {
-        p01 = __fmul2_rn(wyb, make_float2(x.x, x.y));
-        p23 = __fmul2_rn(wyb, make_float2(x.z, x.w));
-      } else {
-        p01 = __ffma2_rn(wyb, make_float2(x.x, x.y), p01);
-        p23 = __ffma2_rn(wyb, make_float2(x.z, x.w), p23);
-      }
-    }
-    const float wzc = DIM == 3 ? pw.wz[c] : 1.f;
-    const float2 wz2 = make_float2(wzc, wzc);
-    if (c == 0) {
-      q01 = __fmul2_rn(wz2, p01);
-      q23 = __fmul2_rn(wz2, p23);
-    } else {
-      q01 = __ffma2_rn(wz2, p01, q01);
-      q23 = __ffma2_rn(wz2, p23, q23);
-    }
-  }
-  const float2 t = __ffma2_rn(make_float2(pw.wx[2], pw.wx[3]), q23,
-                              __fmul2_rn(make_float2(pw.wx[0], pw.wx[1]), q01));
-  return t.x + t.y;
-}
-
-// FP32 extension by chunks (1) or one thread per point (0, the default:
-// measured faster on GB300 at dx = 1/256: 110 us against 198-294 us).
 // FP32 extension, persistent and software-pipelined: a fixed grid of CTAs, each
 // looping over tiles blockIdx.x, blockIdx.x + gridDim.x, ...; while it
 // evaluates the points of one tile from one shared-memory box it has the row
@@ -872,65 +831,83 @@ __global__ void __launch_bounds__(kPipeThreads) k_extend_pipe(LevelView<float> L
 #endif
 constexpr bool kChunked = CPM_EXT_CHUNKED != 0;
 #ifndef CPM_EXT_CHUNK_THREADS
-#define CPM_EXT_CHUNK_THREADS 32
+#define CPM_EXT_CHUNK_THREADS 64
 #endif
 constexpr int kChunkThreads = CPM_EXT_CHUNK_THREADS;
-constexpr int kStageMax = 256;  // points of a tile whose records are staged in shared memory
 
+// One thread per chunk (up to kChunkMax points with one stencil base): the
+// thread streams the base's 4^d stencil rows from the staged box, one 16-byte
+// shared-memory load per row, and accumulates every point of the chunk from
+// each row, in the order of `contract` (y and z first with paired FMAs, then
+// x), so the results equal the per-point kernel's bit for bit.  A chunk of one
+// point repeats it in the second slot and stores it once.
 template <int DIM>
 __global__ void __launch_bounds__(kChunkThreads) k_extend_chunks(LevelView<float> L,
                                                                  const float* __restrict__ u,
                                                                  float* __restrict__ w, bool with_ghost) {
   constexpr int RS = kRS;
-  constexpr int NV = DIM == 3 ? 16 : 4;
+  constexpr int NC = DIM == 3 ? 4 : 1;
   __shared__ TileBox<float, DIM, false> sm;
-  __shared__ uint32_t srec[kStageMax];
-  __shared__ float sfr[DIM][kStageMax];
   const int32_t tile = blockIdx.x;
   const uint32_t tbox = __ldg(L.tile_box + tile);
   const int32_t cbeg = __ldg(L.tile_cstart + tile);
   const int32_t cend = with_ghost ? __ldg(L.tile_cstart + tile + 1) : __ldg(L.tile_cmid + tile);
   if (cbeg == cend) return;  // a tile of ghost points only, extension over B
-  // the tile's records and fractions (a contiguous E-order range), coalesced
-  const int32_t pbeg = __ldg(L.tile_start + tile);
-  const int32_t pend = with_ghost ? __ldg(L.tile_start + tile + 1) : __ldg(L.tile_mid + tile);
-  const bool staged = pend - pbeg <= kStageMax;
-  if (staged)
-    for (int q = threadIdx.x; q < pend - pbeg; q += kChunkThreads) {
-      srec[q] = __ldg(L.erec + pbeg + q);
-#pragma unroll
-      for (int a = 0; a < DIM; ++a) sfr[a][q] = __ldg(L.efr + a * L.nplus + pbeg + q);
-    }
   int32_t c = cbeg + threadIdx.x;
   uint32_t ch = c < cend ? __ldg(L.echunk + c) : 0u;
   stage_box<float, DIM, false, kChunkThreads>(L, u, tile, tbox, sm);
   for (; c < cend; c += kChunkThreads) {
     const int32_t k0 = (int32_t)(ch & 0x3FFFFFFu);
     const int cnt = (int)(ch >> 26) + 1;
-    const int q0 = k0 - pbeg;
-    const uint32_t rec0 = staged ? srec[q0] : __ldg(L.erec + k0);
-    const float* base = sm.win + ((rec0 >> 4) & 3) * 7 * RS + ((rec0 >> 2) & 3) * RS + (rec0 & 3) * 4;
-    float4 v[NV];
+    PointWeights<float, DIM> pw[kChunkMax];
+    uint32_t rec[kChunkMax];
 #pragma unroll
-    for (int q = 0; q < NV; ++q)
-      v[q] = *reinterpret_cast<const float4*>(base + ((q >> 2) * 7 + (q & 3)) * RS);
+    for (int j = 0; j < kChunkMax; ++j) {
+      const int32_t kj = k0 + (j < cnt ? j : 0);
+      rec[j] = __ldg(L.erec + kj);
+      pw[j].load(L, kj);
+    }
     const int32_t cn = c + kChunkThreads;
     if (cn < cend) ch = __ldg(L.echunk + cn);
+    const float* base = sm.win + ((rec[0] >> 4) & 3) * 7 * RS + ((rec[0] >> 2) & 3) * RS + (rec[0] & 3) * 4;
+    float2 q01[kChunkMax], q23[kChunkMax];
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) {
+      float2 p01[kChunkMax], p23[kChunkMax];
+#pragma unroll
+      for (int b = 0; b < 4; ++b) {
+        const float4 v = *reinterpret_cast<const float4*>(base + (cc * 7 + b) * RS);
+#pragma unroll
+        for (int j = 0; j < kChunkMax; ++j) {
+          const float2 wyb = make_float2(pw[j].wy[b], pw[j].wy[b]);
+          if (b == 0) {
+            p01[j] = __fmul2_rn(wyb, make_float2(v.x, v.y));
+            p23[j] = __fmul2_rn(wyb, make_float2(v.z, v.w));
+          } else {
+            p01[j] = __ffma2_rn(wyb, make_float2(v.x, v.y), p01[j]);
+            p23[j] = __ffma2_rn(wyb, make_float2(v.z, v.w), p23[j]);
+          }
+        }
+      }
+#pragma unroll
+      for (int j = 0; j < kChunkMax; ++j) {
+        const float wzc = DIM == 3 ? pw[j].wz[cc] : 1.f;
+        const float2 wz2 = make_float2(wzc, wzc);
+        if (cc == 0) {
+          q01[j] = __fmul2_rn(wz2, p01[j]);
+          q23[j] = __fmul2_rn(wz2, p23[j]);
+        } else {
+          q01[j] = __ffma2_rn(wz2, p01[j], q01[j]);
+          q23[j] = __ffma2_rn(wz2, p23[j], q23[j]);
+        }
+      }
+    }
 #pragma unroll
     for (int j = 0; j < kChunkMax; ++j) {
       if (j < cnt) {
-        uint32_t rec;
-        PointWeights<float, DIM> pw;
-        if (staged) {
-          rec = srec[q0 + j];
-          PointWeights<float, DIM>::cubic(sfr[0][q0 + j], pw.wx);
-          PointWeights<float, DIM>::cubic(sfr[1][q0 + j], pw.wy);
-          if (DIM == 3) PointWeights<float, DIM>::cubic(sfr[DIM == 3 ? 2 : 0][q0 + j], pw.wz);
-        } else {
-          rec = __ldg(L.erec + k0 + j);
-          pw.load(L, k0 + j);
-        }
-        w[rec >> 6] = contract_regs<DIM>(v, pw);
+        const float2 t = __ffma2_rn(make_float2(pw[j].wx[2], pw[j].wx[3]), q23[j],
+                                    __fmul2_rn(make_float2(pw[j].wx[0], pw[j].wx[1]), q01[j]));
+        w[rec[j] >> 6] = t.x + t.y;
       }
     }
   }
