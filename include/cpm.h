@@ -548,12 +548,11 @@ cpm_status cpm_residual_norms(cpm_hier h, const double* f, const double* u, doub
  * Allocation-free form of cpm_residual_norms (the paper has no counterpart).
  *
  * For callers that cannot allocate device memory when they need a residual:
- * work being recorded into a CUDA graph by stream capture (cudaMalloc is
- * refused during a global-mode capture), loops with hard latency budgets that
- * forbid allocator calls, and frameworks that hand out all device memory from
- * their own pool.  It computes r = f - A u on the finest level in FP64 in the
- * direct form (w = E u, then the stencil on w and u; unlike cpm_residual_norms,
- * which uses the relative form described at cpm_residual).  Its rounding floor
+ * loops with hard latency budgets that forbid allocator calls, and frameworks
+ * that hand out all device memory from their own pool.  It computes
+ * r = f - A u on the finest level in FP64 in the direct form (w = E u, then
+ * the stencil on w and u; unlike cpm_residual_norms, which uses the relative
+ * form described at cpm_residual).  Its rounding floor
  * is that of the direct form, about 6 eps |u| / dx^2 in absolute terms; on the
  * levels it accepts (at most 1048576 band + ghost points, dx >= 1/128 for the
  * unit sphere) that is below 1e-12 |M u| for smooth u, so near a converged
@@ -568,13 +567,12 @@ cpm_status cpm_residual_norms(cpm_hier h, const double* f, const double* u, doub
  * scratch (E u on B+ and block partial norms) is one file-scope device array
  * of CPM_NOALLOC_MAX_POINTS doubles plus 8192 doubles (about 8.1 MB), held on
  * every GPU that loads the library until the process exits.  The first call
- * on a device (with that device current) looks up the array's device address
- * once; make that first call before any stream capture.  The looked-up
- * address is cached with the id of the CUDA context that was current, so after
- * cudaDeviceReset (a new context) the next call looks it up again.  Every call shares
- * the one array and overwrites it: calls whose kernels overlap on the GPU
- * (other streams, other host threads) race and must be serialised by the
- * caller.  Nothing in the scratch needs to start at zero.
+ * on a device (with that device current) looks up the array's device address;
+ * the address is cached with the id of the CUDA context that was current, so
+ * after cudaDeviceReset (a new context) the next call looks it up again.
+ * Every call shares the one array and overwrites it: calls whose kernels
+ * overlap on the GPU (other streams, other host threads) race and must be
+ * serialised by the caller.  Nothing in the scratch needs to start at zero.
  * Errors: CPM_ERR_ARG if |B_0| + |G_0| > CPM_NOALLOC_MAX_POINTS (use
  * cpm_residual_norms then) or on NULL arguments.
  */

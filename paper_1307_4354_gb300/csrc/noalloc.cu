@@ -1,10 +1,9 @@
 // Allocation-free residual norms of the finest level (cpm_residual_norms_noalloc).
 //
 // Some callers cannot allocate device memory at the moment they need the
-// residual: work recorded into a CUDA graph by stream capture (cudaMalloc is
-// refused inside a global-mode capture), loops with hard latency budgets that
-// forbid allocator calls, and host frameworks that hand out every byte of
-// device memory from their own pool.  This entry point therefore allocates
+// residual: loops with hard latency budgets that forbid allocator calls, and
+// host frameworks that hand out every byte of device memory from their own
+// pool.  This entry point therefore allocates
 // nothing and leaves the hierarchy's own work buffers alone: its scratch (the
 // extension E u on B+ and the per-block partial norms) is one file-scope
 // device array of fixed size, resident on every GPU that loads the library
