@@ -405,7 +405,7 @@ __global__ void __launch_bounds__(256) k_resid_pair(LevelView<double> L, const d
 #pragma unroll
   for (int j = 0; j < kPairPts; ++j) {
     const int32_t i = (blockIdx.x * kPairPts + j) * blockDim.x + threadIdx.x;
-    if (i >= L.nB) break;
+    if (i >= L.nB) continue;  // (not break: the points' loads can then overlap)
     int32_t k[2 * DIM];
 #pragma unroll
     for (int q = 0; q < 2 * DIM; ++q) k[q] = __ldg(L.nbr + (int64_t)q * L.nB + i);
