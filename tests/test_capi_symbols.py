@@ -14,10 +14,11 @@ def _declared():
     return sorted(set(re.findall(r"\b(cpm_[a-z0-9_]+)\s*\(", src)))
 
 
-def test_header_declares_the_north_star_entry_points():
+def test_header_declares_the_solver_entry_points():
     names = _declared()
     for n in ["cpm_build_band", "cpm_build_hierarchy", "cpm_apply", "cpm_smooth", "cpm_vcycle",
-              "cpm_solve"]:
+              "cpm_solve", "cpm_residual", "cpm_solve_batch", "cpm_mlp_train", "cpm_mlp_save",
+              "cpm_mlp_load"]:
         assert n in names
 
 
