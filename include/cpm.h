@@ -455,7 +455,8 @@ typedef struct cpm_solve_report {
  * full FP64 evaluation of the same iterate, and if that misses the tolerance
  * the rest of the solve uses FP64 residuals.  Synchronous (reads the
  * residual norms once per outer iteration).  report may be NULL.
- * Errors: CPM_ERR_NOT_CONVERGED, CPM_ERR_DIVERGED (u holds the last iterate).
+ * Errors: CPM_ERR_ARG (NULL arguments, bad options, a NaN or infinity in f),
+ * CPM_ERR_NOT_CONVERGED, CPM_ERR_DIVERGED (u holds the last iterate).
  */
 cpm_status cpm_solve(cpm_hier h, const double* f, double* u, const cpm_solve_opts* opts,
                      cpm_solve_report* report, cpm_stream stream);

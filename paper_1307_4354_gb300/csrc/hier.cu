@@ -1238,7 +1238,7 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
     CPM_CUDA_TRY(cudaMemcpyAsync(W.u_own.get(), u, nB * sizeof(double), cudaMemcpyDeviceToDevice, st));
   launch_norm_partials<double>(W.f_own.get(), nB, W.part.get(), st);
   launch_norm_final(W.part.get(), kNormBlocks, W.normf.get(), st);
-  CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned + 4, W.normf.get(), sizeof(double), cudaMemcpyDeviceToHost, st));
+  CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned + 4, W.normf.get(), 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
   if (o.zero_init) {  // u = 0: the residual is f itself, and so are its norms
     CPM_CUDA_TRY(cudaMemcpyAsync(W.r64.get(), W.f_own.get(), nB * sizeof(double),
                                  cudaMemcpyDeviceToDevice, st));
@@ -1249,7 +1249,9 @@ static cpm_status solve_ws(cpm_hier h, Workspace& W, const double* f, double* u,
   CPM_CUDA_TRY(cudaMemcpyAsync(W.pinned, W.norms, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CPM_CUDA_TRY(cudaStreamSynchronize(st));
   const double fmax = W.pinned[4];
-  CPM_CHECK(std::isfinite(fmax), CPM_ERR_ARG, "f is not finite");
+  // the maximum skips NaN (fmax), the sum of squares does not (it may still
+  // overflow to infinity for a finite f, so only NaN is tested there)
+  CPM_CHECK(std::isfinite(fmax) && !std::isnan(W.pinned[5]), CPM_ERR_ARG, "f is not finite");
   const double fn = fmax > 0 ? fmax : 1.0;
   CPM_CHECK(!o.learned || (o.mode == CPM_SOLVE_MIXED && h->mlp), CPM_ERR_ARG,
             "learned smoothing needs mode MIXED and cpm_hier_set_smoother");
@@ -1875,7 +1877,8 @@ cpm_status cpm_solve_batch(cpm_batch b, const double* const* f, double* const* u
   std::vector<double> fmax(ns), rel(ns), best(ns), prev(ns);
   std::vector<int> done(ns, 0);
   for (int s = 0; s < ns; ++s) {
-    CPM_CHECK(std::isfinite(hf[4 * (size_t)s]), CPM_ERR_ARG, "f is not finite");
+    CPM_CHECK(std::isfinite(hf[4 * (size_t)s]) && !std::isnan(hf[4 * (size_t)s + 1]), CPM_ERR_ARG,
+              "f is not finite");
     fmax[s] = hf[4 * (size_t)s] > 0 ? hf[4 * (size_t)s] : 1.0;
     rel[s] = best[s] = prev[s] = b->host_norms[4 * (size_t)s] / fmax[s];
   }

@@ -69,3 +69,23 @@ def test_graph_and_plain_launches_agree():
         u2, r2 = H.solve(ft, tol=1e-10, mode=mode, use_graph=False)
         assert r1["iters"] == r2["iters"]
         assert torch.equal(u1, u2)
+
+
+def test_solve_edge_cases_zero_and_non_finite_rhs():
+    """f = 0: the solution u = 0 is returned at iteration 0 with a zero residual.
+    A NaN or an infinity in f is rejected with CPM_ERR_ARG (the maximum of |f|
+    skips NaN, so the sum of squares is checked as well), not run to divergence."""
+    torch, pkg = require_cuda()
+    g = pkg.Band("circle", (), 1 / 32)
+    H = pkg.Hierarchy(g, coarsest_dx=1 / 8)
+    f0 = torch.zeros(g.nb, dtype=torch.float64, device="cuda")
+    for mode in ("f64", "mixed"):
+        u, rep = H.solve(f0, tol=1e-10, mode=mode)
+        assert rep["converged"] and rep["iters"] == 0 and rep["rel_residual"] == 0.0, rep
+        assert float(u.abs().max()) == 0.0
+    for bad in (float("nan"), float("inf")):
+        f = torch.ones(g.nb, dtype=torch.float64, device="cuda")
+        f[g.nb // 2] = bad
+        with pytest.raises(pkg.capi.CpmError) as e:
+            H.solve(f, tol=1e-10, mode="mixed")
+        assert e.value.status == pkg.capi.CPM_ERR_ARG
